@@ -1,0 +1,223 @@
+/*
+ * rpiv.h - C ABI of librpiv, a GB300 (sm_103a) implementation of the
+ * correction hot path of RapidPIV (Bollt, Foxman, Gharib, arXiv 2504.17987).
+ *
+ * What the library computes (paper Sec. 2, "RapidPIV"): for an image pair
+ * (A, B) and a displacement predictor, frame B is warped by the predictor
+ * (bilinear image deformation), each interrogation window of A is correlated
+ * against the warped B with the zero-normalised correlation coefficient over
+ * a +-r integer search, the integer peak is refined by a three-point Gaussian
+ * fit per axis, the universal outlier detector (normalised median test,
+ * threshold 2, regulariser 0.1 px in Sec. 3.1/3.2) flags outliers and replaces
+ * them by the median of their non-outlier neighbours, and vorticity is derived
+ * from the final field.  The paper obtains the predictor from a fixed-function
+ * optical-flow engine; here a coarse-to-fine correlation pyramid (2x2 box
+ * levels) computed by the same kernels stands in for it, or the caller
+ * supplies one (e.g. the previous field of a camera stream).  r = 0 is the
+ * paper's fixed 5-point stencil centred on the predicted displacement.
+ *
+ * Conventions for every entry point
+ *   - Image and field pointers are DEVICE pointers owned by the caller unless
+ *     stated; they must stay valid until the work enqueued on `cuda_stream`
+ *     has completed.  The handle owns only its workspace, streams, events and
+ *     captured CUDA graphs.
+ *   - Images are single-channel, row-major, `pitch_bytes` between rows
+ *     (pitch_bytes >= width * bytes per pixel); uint8 or uint16 (12-bit data
+ *     is stored LSB-aligned, 0..4095).  x = column, y = row (downwards).
+ *   - Vector grids of window w and step s = w (1 - overlap) have
+ *     nx = floor((W - w)/s) + 1 columns and ny rows; node (i, j) sits at the
+ *     window centre (i s + (w-1)/2, j s + (w-1)/2); arrays are ny x nx
+ *     row-major float32 (u, v in px/frame, vorticity in 1/frame), the mask is
+ *     uint8 (1 = passed the outlier test, 0 = flagged/replaced or invalid).
+ *   - Work is enqueued asynchronously on `cuda_stream` (a cudaStream_t; NULL
+ *     = the legacy default stream).  Nothing synchronises except
+ *     rpiv_destroy.  Calls on one handle must not run concurrently from
+ *     several host threads; the handle orders its own launches so that calls
+ *     on different streams do not overlap on the device.
+ *   - Nothing throws across the ABI.  Every call returns an rpiv_status;
+ *     rpiv_last_error() gives a human-readable message for the calling thread.
+ */
+#ifndef RPIV_H
+#define RPIV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RPIV_MAX_PASSES 4
+#define RPIV_MAX_BATCH 64
+#define RPIV_MAX_RADIUS 16
+#define RPIV_MAX_LEVELS 4
+
+typedef enum {
+    RPIV_OK = 0,
+    RPIV_ERR_INVALID_ARG = 1, /* a null pointer, a size or parameter out of range */
+    RPIV_ERR_UNSUPPORTED = 2, /* valid request this build does not implement     */
+    RPIV_ERR_OOM = 3,         /* device or pinned host allocation failed         */
+    RPIV_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has detail) */
+    RPIV_ERR_TIMEOUT = 5,     /* rpiv_wait gave up before the work completed      */
+    RPIV_ERR_BUSY = 6,        /* reserved                                        */
+    RPIV_ERR_NO_DEVICE = 7    /* no usable CUDA device                           */
+} rpiv_status;
+
+typedef enum { RPIV_U8 = 1, RPIV_U16 = 2 } rpiv_pixfmt;
+
+/* Arithmetic of the correlation plane.  The argmax is taken on this plane;
+ * the 5-point stencil for the Gaussian fit is always recomputed in FP32.  */
+typedef enum { RPIV_FP32 = 0, RPIV_BF16 = 1, RPIV_FP16 = 2 } rpiv_precision;
+
+/* Image deformation: frame B only (B'(x) = B(x + d(x)), default) or central
+ * (A'(x) = A(x - d/2), B'(x) = B(x + d/2), the paper's "central difference"). */
+typedef enum { RPIV_DEFORM_B = 0, RPIV_DEFORM_CENTRAL = 1 } rpiv_deform;
+
+typedef struct {
+    int width, height;          /* image size, px                                  */
+    rpiv_pixfmt fmt;            /* RPIV_U8 or RPIV_U16                              */
+    int bit_depth;              /* 8, 12 or 16 (informational; no rescaling)        */
+    int n_passes;               /* full-resolution passes, 1..RPIV_MAX_PASSES       */
+    int window[RPIV_MAX_PASSES];     /* even, 8..128, in pass order                 */
+    float overlap[RPIV_MAX_PASSES];  /* [0, 1); w (1 - overlap) must be an integer  */
+    int search_radius[RPIV_MAX_PASSES]; /* 0..RPIV_MAX_RADIUS                       */
+    int predictor_levels;       /* coarse-to-fine pyramid levels (0 = zero or caller
+                                   predictor); each level runs a pass with
+                                   window[0], overlap[0], search_radius[0]          */
+    float uod_threshold;        /* normalised-median threshold (paper: 2)          */
+    float uod_eps;              /* regulariser, px (paper: 0.1)                     */
+    int replace_outliers;       /* 1: replace by neighbour median; 0: flag only    */
+    rpiv_precision precision;   /* correlation-plane arithmetic                    */
+    rpiv_deform deform_mode;    /* RPIV_DEFORM_B (default) or RPIV_DEFORM_CENTRAL   */
+    int max_batch;              /* 1..RPIV_MAX_BATCH pairs per rpiv_process_batch   */
+} rpiv_config;
+
+typedef struct rpiv_handle rpiv_handle;
+
+/* Fills *cfg with the paper's settings for a 1 MP 8-bit pair: 16 px windows,
+ * 50 % overlap (Sec. 3.1, 4.1), UOD threshold 2 / 0.1 px, r = 1, FP32,
+ * frame-B deformation, no pyramid, max_batch 1.                              */
+rpiv_status rpiv_config_default(rpiv_config *cfg);
+
+/* Host-only validation of a configuration (no device access).  On success
+ * writes the final-pass grid size.  Rejects: null pointers, image smaller than
+ * window + 2 (radius + 1) at any level, odd or out-of-range windows, overlap
+ * outside [0, 1) or a non-integer step, radius outside [0, 16], more than
+ * 4 passes or levels, batch outside [1, 64], unknown enums.                  */
+rpiv_status rpiv_validate_config(const rpiv_config *cfg, int *nx, int *ny);
+
+/* Creates a handle on CUDA device `device`: validates cfg, allocates the
+ * workspace for cfg->max_batch pairs (pyramid levels and per-stage fields)
+ * and a pinned host ring for per-call pointer tables.  *out is set only on
+ * RPIV_OK.  Errors: INVALID_ARG, NO_DEVICE, OOM, CUDA.                       */
+rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out);
+
+/* Final-pass grid size of a handle.                                          */
+rpiv_status rpiv_grid_shape(const rpiv_handle *h, int *nx, int *ny);
+
+/* Device bytes the handle holds (workspace), for admission control.         */
+rpiv_status rpiv_workspace_bytes(const rpiv_handle *h, size_t *bytes);
+
+/* One image pair through the whole schedule (pyramid or caller predictor,
+ * every pass with deformation, correlation, peak, Gaussian fit and outlier
+ * test, vorticity).
+ *   img_a, img_b   device images, fmt of the config, pitch_bytes apart rows.
+ *   pred_u, pred_v nullable device arrays on the FINAL-pass grid: when given
+ *                  they replace the pyramid as the predictor of pass 1
+ *                  (interpolated onto its grid).  Both or neither.
+ *   u, v, vort     device float arrays, ny x nx of the final pass.
+ *   mask           device uint8 array, ny x nx.  vort and mask may be NULL.
+ * Errors: INVALID_ARG (nulls, pitch too small), CUDA.                        */
+rpiv_status rpiv_process_pair(rpiv_handle *h, const void *img_a, const void *img_b, size_t pitch_bytes,
+                              const float *pred_u, const float *pred_v, float *u, float *v, float *vort,
+                              uint8_t *mask, void *cuda_stream);
+
+/* n pairs of the handle's size and format in one launch sequence (pairs are
+ * independent; the batch index only selects data).  Every pointer argument
+ * is a HOST array of n device pointers; pred_u/pred_v may be NULL (no pair
+ * has a predictor) or hold NULL entries (that pair uses the pyramid), vort
+ * and mask may be NULL or hold NULL entries.  Launch sequences are captured
+ * once per (n, predictor pattern) as a CUDA graph and replayed.
+ * Errors: INVALID_ARG (n outside [1, max_batch], nulls), CUDA.               */
+rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, const void *const *img_b,
+                               size_t pitch_bytes, const float *const *pred_u, const float *const *pred_v,
+                               float *const *u, float *const *v, float *const *vort, uint8_t *const *mask,
+                               void *cuda_stream);
+
+/* Score S = sum over the windows of pass 1's grid (window[0], overlap[0]) of
+ * the zero-shift correlation coefficient between A and B warped by the field
+ * (u, v) on that grid (frame-B deformation), and its adjoint
+ *     grad_u = grad_score * dS/du,  grad_v = grad_score * dS/dv,
+ * through the bilinear image interpolation and the bilinear field-to-pixel
+ * weights (deformed windows are recomputed, not stored).  grad_u/grad_v may
+ * both be NULL (score only); score_out (device float) may be NULL.  The
+ * gradient is accumulated deterministically (no floating-point atomics).
+ * Errors: INVALID_ARG, CUDA.                                                 */
+rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, size_t pitch_bytes,
+                          const float *u, const float *v, float grad_score, float *grad_u, float *grad_v,
+                          float *score_out, void *cuda_stream);
+
+/* Blocks until the handle's enqueued work has finished, polling for at most
+ * timeout_ms milliseconds (host watchdog).  RPIV_ERR_TIMEOUT if it has not.  */
+rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms);
+
+/* Synchronises and frees everything the handle owns.  NULL is a no-op.      */
+rpiv_status rpiv_destroy(rpiv_handle *h);
+
+/* Message describing the last failing call on this thread ("" if none).
+ * Valid until the next rpiv_* call on the same thread.                      */
+const char *rpiv_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points.  Each runs one step of the method on caller buffers
+ * (device pointers, one pair, enqueued on cuda_stream) with the same kernels
+ * the handle uses; they exist for stage-by-stage verification and for
+ * callers composing their own schedules.  No handle and no allocation.
+ * ---------------------------------------------------------------------- */
+
+/* One correlation pass (paper Sec. 2: warp, correlation coefficient around
+ * the peak, Gaussian sub-pixel fit) on the grid (w, step) of a W x H image.
+ *   fmt        RPIV_U8, RPIV_U16, or 0 for float32 images (pyramid levels).
+ *   pred_u/v   predictor on this grid's nodes (device, ny x nx float).
+ *   u, v       raw (pre-validation) result, ny x nx float.
+ *   info       ny x nx int32: bit 0 valid window, bits 8..15 the integer peak
+ *              ky and bits 16..23 kx as int8.
+ * Errors: INVALID_ARG (sizes, nulls, radius), UNSUPPORTED (precision not
+ * built for this radius), CUDA.                                              */
+rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int width,
+                                 int height, int window, int step, int radius, rpiv_precision precision,
+                                 rpiv_deform deform_mode, const float *pred_u, const float *pred_v, float *u,
+                                 float *v, int32_t *info, void *cuda_stream);
+
+/* Normalised median test + median replacement (paper Sec. 2, Westerweel &
+ * Scarano 2005) on an nx x ny field; info (nullable) marks invalid windows
+ * (bit 0 clear) which are always treated as outliers.  Writes u_out, v_out
+ * and mask (1 passed, 0 flagged).  Input and output arrays must not alias.  */
+rpiv_status rpiv_stage_validate(const float *u, const float *v, const int32_t *info, int nx, int ny,
+                                float threshold, float eps, int replace, float *u_out, float *v_out,
+                                uint8_t *mask, void *cuda_stream);
+
+/* Bilinear interpolation of a source grid field (snx x sny, window sw, step
+ * ss) onto the nodes of a destination grid (dnx x dny, window dw, step ds)
+ * whose image is `levels_up` pyramid levels finer (position map
+ * x_src = (x_dst + 0.5)/2^L - 0.5, values times 2^L).  Outside the source node
+ * hull the border value is extended.                                         */
+rpiv_status rpiv_stage_interp(const float *su, const float *sv, int snx, int sny, int sw, int ss, float *du,
+                              float *dv, int dnx, int dny, int dw, int ds, int levels_up, void *cuda_stream);
+
+/* omega = dv/dx - du/dy on an nx x ny grid of step s: central differences
+ * inside, one-sided on the border, zero along an axis with one node.        */
+rpiv_status rpiv_stage_vorticity(const float *u, const float *v, int nx, int ny, int step, float *vort,
+                                 void *cuda_stream);
+
+/* 2x2 box average of a W x H image (fmt RPIV_U8, RPIV_U16 or 0 = float32,
+ * pitch in bytes) into a floor(W/2) x floor(H/2) float32 image, row-major
+ * without padding.                                                          */
+rpiv_status rpiv_stage_downsample(const void *img, size_t pitch_bytes, int fmt, int width, int height,
+                                  float *out, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPIV_H */

@@ -1,0 +1,787 @@
+// C ABI of librpiv (declared in include/rpiv.h): configuration checks, the
+// per-handle schedule of stages (pyramid levels, passes), device workspace,
+// per-call pointer tables and the CUDA-graph cache.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rpiv.h"
+#include "rpiv_internal.h"
+
+using namespace rpiv;
+
+namespace rpiv {
+void prepare_pass_kernels();
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+rpiv_status fail(rpiv_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+rpiv_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return RPIV_ERR_CUDA;
+}
+
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+int grid_n(int extent, int w, int s) { return (extent < w || w < 1 || s < 1) ? 0 : (extent - w) / s + 1; }
+
+bool step_of(int w, float overlap, int *s)
+{
+    const double sd = (double)w * (1.0 - (double)overlap);
+    const int si = (int)std::lround(sd);
+    if (si < 1 || std::fabs(sd - si) > 1e-4) return false;
+    *s = si;
+    return true;
+}
+
+int prec_of(rpiv_precision p) { return p == RPIV_FP32 ? PREC_FP32 : (p == RPIV_BF16 ? PREC_BF16 : PREC_FP16); }
+
+struct StageDef {
+    bool level;  // pyramid level (float images in the workspace) or full-resolution pass
+    int lvl;     // pyramid level index (0 for passes)
+    int W, H;    // image size of this stage
+    int w, s, R;
+    int nx, ny;
+    int prec;
+    size_t off_pred, off_raw, off_info, off_out, off_mask;  // per-pair workspace offsets
+    PassPlan plan;
+};
+
+std::string check_config(const rpiv_config *c, std::vector<StageDef> *stages_out)
+{
+    if (!c) return "config is NULL";
+    if (c->fmt != RPIV_U8 && c->fmt != RPIV_U16) return "fmt must be RPIV_U8 or RPIV_U16";
+    if (c->bit_depth != 8 && c->bit_depth != 12 && c->bit_depth != 16) return "bit_depth must be 8, 12 or 16";
+    if (c->fmt == RPIV_U8 && c->bit_depth != 8) return "RPIV_U8 requires bit_depth 8";
+    if (c->n_passes < 1 || c->n_passes > RPIV_MAX_PASSES) return "n_passes must be in [1, 4]";
+    if (c->predictor_levels < 0 || c->predictor_levels > RPIV_MAX_LEVELS) return "predictor_levels must be in [0, 4]";
+    if (c->max_batch < 1 || c->max_batch > RPIV_MAX_BATCH) return "max_batch must be in [1, 64]";
+    if (c->precision != RPIV_FP32 && c->precision != RPIV_BF16 && c->precision != RPIV_FP16)
+        return "unknown precision";
+    if (c->deform_mode != RPIV_DEFORM_B && c->deform_mode != RPIV_DEFORM_CENTRAL) return "unknown deform_mode";
+    if (!(c->uod_threshold > 0.f) || !(c->uod_eps >= 0.f) || !std::isfinite(c->uod_threshold) ||
+        !std::isfinite(c->uod_eps))
+        return "uod_threshold must be > 0 and uod_eps >= 0";
+    if (c->width < 8 || c->height < 8 || c->width > 65536 || c->height > 65536) return "image size out of range";
+    for (int p = 0; p < c->n_passes; ++p) {
+        const int w = c->window[p];
+        if (w < 8 || w > 128 || (w & 1)) return "window[" + std::to_string(p) + "] must be even and in [8, 128]";
+        if (!(c->overlap[p] >= 0.f && c->overlap[p] < 1.f)) return "overlap must be in [0, 1)";
+        int s;
+        if (!step_of(w, c->overlap[p], &s)) return "window * (1 - overlap) must be a positive integer";
+        const int R = c->search_radius[p];
+        if (R < 0 || R > RPIV_MAX_RADIUS) return "search_radius must be in [0, 16]";
+    }
+    std::vector<StageDef> st;
+    {
+        int s0 = 1;
+        step_of(c->window[0], c->overlap[0], &s0);
+        int W = c->width, H = c->height;
+        std::vector<StageDef> lv;
+        for (int l = 1; l <= c->predictor_levels; ++l) {
+            W /= 2;
+            H /= 2;
+            StageDef d{};
+            d.level = true;
+            d.lvl = l;
+            d.W = W;
+            d.H = H;
+            d.w = c->window[0];
+            d.s = s0;
+            d.R = c->search_radius[0];
+            lv.push_back(d);
+        }
+        for (int i = (int)lv.size() - 1; i >= 0; --i) st.push_back(lv[i]);  // coarsest first
+    }
+    for (int p = 0; p < c->n_passes; ++p) {
+        StageDef d{};
+        d.level = false;
+        d.W = c->width;
+        d.H = c->height;
+        d.w = c->window[p];
+        step_of(d.w, c->overlap[p], &d.s);
+        d.R = c->search_radius[p];
+        st.push_back(d);
+    }
+    for (auto &d : st) {
+        if (d.W < d.w + 2 * (d.R + 1) || d.H < d.w + 2 * (d.R + 1))
+            return std::string(d.level ? "pyramid level " + std::to_string(d.lvl) : std::string("image")) + " of " +
+                   std::to_string(d.W) + "x" + std::to_string(d.H) + " is smaller than window + 2 (radius + 1)";
+        d.nx = grid_n(d.W, d.w, d.s);
+        d.ny = grid_n(d.H, d.w, d.s);
+        // a zero radius has a one-point plane: the FP32 kernel serves every precision
+        d.prec = d.R == 0 ? PREC_FP32 : prec_of(c->precision);
+        if (!pass_plan(d.w, d.s, d.R, d.nx, d.ny, d.prec, &d.plan))
+            return "precision " + std::to_string((int)c->precision) + " is not built for radius " +
+                   std::to_string(d.R) + " with window " + std::to_string(d.w) + " and step " + std::to_string(d.s);
+    }
+    if (stages_out) *stages_out = st;
+    return "";
+}
+
+constexpr int kRing = 16;
+
+}  // namespace
+
+struct rpiv_handle {
+    rpiv_config cfg{};
+    int device = 0;
+    std::vector<StageDef> stages;
+    size_t pyr_off[RPIV_MAX_LEVELS + 1][2] = {};  // per-pair offsets of pyramid A/B images (level >= 1)
+    size_t pair_stride = 0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    PairIO *io_dev = nullptr;
+    PairIO *ring = nullptr;  // pinned host, kRing slots of max_batch entries
+    cudaEvent_t ring_ev[kRing] = {};
+    bool ring_used[kRing] = {};
+    int ring_pos = 0;
+    cudaEvent_t done_ev = nullptr;
+    bool done_recorded = false;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, cudaGraphExec_t> graphs;
+    char *adj_ws = nullptr;
+    size_t adj_bytes = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// The full schedule for n pairs whose pointers are in h->io_dev.
+rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred, bool any_nopred, cudaStream_t st)
+{
+    const rpiv_config &c = h->cfg;
+    const int L = c.predictor_levels;
+    const long long ps = (long long)h->pair_stride;
+    const PairIO *io = h->io_dev;
+    const long long ios = sizeof(PairIO);
+    auto ws = [&](size_t off) { return ptr_direct(h->ws + off, ps); };
+    auto tab = [&](const void *field) { return ptr_table(field, ios); };
+    const int user_fmt = c.fmt == RPIV_U8 ? PIX_U8 : PIX_U16;
+    const StageDef &p0 = h->stages[L];
+    const bool run_pyr = L > 0 && any_nopred;
+
+    auto run_pass = [&](const StageDef &d, PtrRef A, PtrRef B, int fmt, long long pch, bool pred) -> rpiv_status {
+        PassArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.W = d.W;
+        a.H = d.H;
+        a.fmt = fmt;
+        a.pitch = pch;
+        a.img_a = A;
+        a.img_b = B;
+        a.w = d.w;
+        a.s = d.s;
+        a.R = d.R;
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.deform = c.deform_mode == RPIV_DEFORM_CENTRAL ? 1 : 0;
+        a.prec = d.prec;
+        const size_t n1 = (size_t)d.nx * d.ny;
+        a.pred_u = pred ? ws(d.off_pred) : ptr_direct(nullptr, 0);
+        a.pred_v = pred ? ws(d.off_pred + 4 * n1) : ptr_direct(nullptr, 0);
+        a.out_u = ws(d.off_raw);
+        a.out_v = ws(d.off_raw + 4 * n1);
+        a.out_info = ws(d.off_info);
+        a.plan = d.plan;
+        CK(launch_pass(a, n, st), "correlation pass launch");
+        return RPIV_OK;
+    };
+    auto run_uod = [&](const StageDef &d, bool final_stage) -> rpiv_status {
+        UodArgs u;
+        const size_t n1 = (size_t)d.nx * d.ny;
+        u.u = ws(d.off_raw);
+        u.v = ws(d.off_raw + 4 * n1);
+        u.info = ws(d.off_info);
+        u.nx = d.nx;
+        u.ny = d.ny;
+        u.thr = c.uod_threshold;
+        u.eps = c.uod_eps;
+        u.replace = c.replace_outliers ? 1 : 0;
+        if (final_stage) {
+            u.u_out = tab(&io[0].u);
+            u.v_out = tab(&io[0].v);
+            u.mask = tab(&io[0].mask);
+        } else {
+            u.u_out = ws(d.off_out);
+            u.v_out = ws(d.off_out + 4 * n1);
+            u.mask = ws(d.off_mask);
+        }
+        CK(launch_uod(u, n, st), "outlier test launch");
+        return RPIV_OK;
+    };
+    auto run_interp = [&](const StageDef &src, PtrRef su, PtrRef sv, const StageDef &dst, int lv_up,
+                          int zero_if_null) -> rpiv_status {
+        InterpArgs ia;
+        const size_t nd = (size_t)dst.nx * dst.ny;
+        ia.su = su;
+        ia.sv = sv;
+        ia.snx = src.nx;
+        ia.sny = src.ny;
+        ia.sw = src.w;
+        ia.ss = src.s;
+        ia.du = ws(dst.off_pred);
+        ia.dv = ws(dst.off_pred + 4 * nd);
+        ia.dnx = dst.nx;
+        ia.dny = dst.ny;
+        ia.dw = dst.w;
+        ia.ds = dst.s;
+        ia.levels_up = lv_up;
+        ia.zero_if_null = zero_if_null;
+        CK(launch_interp(ia, n, st), "interpolation launch");
+        return RPIV_OK;
+    };
+    rpiv_status rs;
+
+    bool pass0_pred = false;
+    if (run_pyr) {
+        for (int l = 1; l <= L; ++l) {
+            for (int ab = 0; ab < 2; ++ab) {
+                DownArgs d;
+                if (l == 1) {
+                    d.src = tab(ab ? (const void *)&io[0].b : (const void *)&io[0].a);
+                    d.fmt = user_fmt;
+                    d.pitch = (long long)pitch;
+                    d.W = c.width;
+                    d.H = c.height;
+                } else {
+                    const StageDef &prev = h->stages[L - (l - 1)];
+                    d.src = ws(h->pyr_off[l - 1][ab]);
+                    d.fmt = PIX_F32;
+                    d.pitch = (long long)prev.W * 4;
+                    d.W = prev.W;
+                    d.H = prev.H;
+                }
+                d.dst = ws(h->pyr_off[l][ab]);
+                CK(launch_down(d, n, st), "pyramid launch");
+            }
+        }
+        for (int i = 0; i < L; ++i) {
+            const StageDef &d = h->stages[i];
+            const bool pred = i > 0;
+            if (pred) {
+                const StageDef &prev = h->stages[i - 1];
+                const size_t np = (size_t)prev.nx * prev.ny;
+                if ((rs = run_interp(prev, ws(prev.off_out), ws(prev.off_out + 4 * np), d, 1, 0)) != RPIV_OK) return rs;
+            }
+            if ((rs = run_pass(d, ws(h->pyr_off[d.lvl][0]), ws(h->pyr_off[d.lvl][1]), PIX_F32, (long long)d.W * 4,
+                               pred)) != RPIV_OK)
+                return rs;
+            if ((rs = run_uod(d, false)) != RPIV_OK) return rs;
+        }
+        const StageDef &l1 = h->stages[L - 1];
+        const size_t n1 = (size_t)l1.nx * l1.ny;
+        if ((rs = run_interp(l1, ws(l1.off_out), ws(l1.off_out + 4 * n1), p0, 1, 0)) != RPIV_OK) return rs;
+        pass0_pred = true;
+    }
+    if (any_pred) {
+        // caller predictor on the final-pass grid; pairs without one keep the
+        // pyramid result, or get zero when there is no pyramid
+        const StageDef &fin = h->stages.back();
+        if ((rs = run_interp(fin, tab(&io[0].pred_u), tab(&io[0].pred_v), p0, 0, run_pyr ? 0 : 1)) != RPIV_OK)
+            return rs;
+        pass0_pred = true;
+    }
+    const int np = c.n_passes;
+    for (int p = 0; p < np; ++p) {
+        const StageDef &d = h->stages[L + p];
+        bool pred = (p == 0) ? pass0_pred : true;
+        if (p > 0) {
+            const StageDef &prev = h->stages[L + p - 1];
+            const size_t nprev = (size_t)prev.nx * prev.ny;
+            if ((rs = run_interp(prev, ws(prev.off_out), ws(prev.off_out + 4 * nprev), d, 0, 0)) != RPIV_OK) return rs;
+        }
+        if ((rs = run_pass(d, tab(&io[0].a), tab(&io[0].b), user_fmt, (long long)pitch, pred)) != RPIV_OK) return rs;
+        if ((rs = run_uod(d, p == np - 1)) != RPIV_OK) return rs;
+        if (p < np - 1) {
+            // the next pass reads this pass's validated field from the workspace
+        }
+    }
+    const StageDef &fin = h->stages.back();
+    VortArgs va;
+    va.u = tab(&io[0].u);
+    va.v = tab(&io[0].v);
+    va.out = tab(&io[0].vort);
+    va.nx = fin.nx;
+    va.ny = fin.ny;
+    va.s = fin.s;
+    CK(launch_vort(va, n, st), "vorticity launch");
+    return RPIV_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+
+extern "C" {
+
+const char *rpiv_last_error(void) { return g_err.c_str(); }
+
+rpiv_status rpiv_config_default(rpiv_config *cfg)
+{
+    if (!cfg) return fail(RPIV_ERR_INVALID_ARG, "cfg is NULL");
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->width = 1024;
+    cfg->height = 1024;
+    cfg->fmt = RPIV_U8;
+    cfg->bit_depth = 8;
+    cfg->n_passes = 1;
+    cfg->window[0] = 16;
+    cfg->overlap[0] = 0.5f;
+    cfg->search_radius[0] = 1;
+    cfg->predictor_levels = 0;
+    cfg->uod_threshold = 2.0f;
+    cfg->uod_eps = 0.1f;
+    cfg->replace_outliers = 1;
+    cfg->precision = RPIV_FP32;
+    cfg->deform_mode = RPIV_DEFORM_B;
+    cfg->max_batch = 1;
+    g_err.clear();
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_validate_config(const rpiv_config *cfg, int *nx, int *ny)
+{
+    std::vector<StageDef> st;
+    const std::string msg = check_config(cfg, &st);
+    if (!msg.empty()) return fail(RPIV_ERR_INVALID_ARG, msg);
+    if (nx) *nx = st.back().nx;
+    if (ny) *ny = st.back().ny;
+    g_err.clear();
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
+{
+    if (!out) return fail(RPIV_ERR_INVALID_ARG, "out is NULL");
+    std::vector<StageDef> st;
+    const std::string msg = check_config(cfg, &st);
+    if (!msg.empty()) return fail(RPIV_ERR_INVALID_ARG, msg);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(RPIV_ERR_NO_DEVICE, "no CUDA device");
+    }
+    if (device < 0 || device >= ndev) return fail(RPIV_ERR_INVALID_ARG, "device index out of range");
+    DeviceGuard dg(device);
+    prepare_pass_kernels();
+    rpiv_handle *h = new rpiv_handle();
+    h->cfg = *cfg;
+    h->device = device;
+    h->stages = st;
+    // per-pair workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = up(off + bytes, 256);
+        return o;
+    };
+    {
+        int W = cfg->width, H = cfg->height;
+        for (int l = 1; l <= cfg->predictor_levels; ++l) {
+            W /= 2;
+            H /= 2;
+            h->pyr_off[l][0] = take((size_t)W * H * 4);
+            h->pyr_off[l][1] = take((size_t)W * H * 4);
+        }
+    }
+    for (auto &d : h->stages) {
+        const size_t n1 = (size_t)d.nx * d.ny;
+        d.off_pred = take(8 * n1);
+        d.off_raw = take(8 * n1);
+        d.off_info = take(4 * n1);
+        d.off_out = take(8 * n1);
+        d.off_mask = take(n1);
+    }
+    h->pair_stride = up(off, 256);
+    h->ws_bytes = h->pair_stride * cfg->max_batch;
+    auto cleanup = [&](rpiv_status s, const std::string &m) {
+        rpiv_destroy(h);
+        return fail(s, m);
+    };
+    cudaError_t e = cudaMalloc(&h->ws, h->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(RPIV_ERR_OOM, "workspace allocation of " + std::to_string(h->ws_bytes) + " bytes failed");
+    }
+    e = cudaMalloc(&h->io_dev, sizeof(PairIO) * cfg->max_batch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(RPIV_ERR_OOM, "pointer table allocation failed");
+    }
+    e = cudaHostAlloc(&h->ring, sizeof(PairIO) * cfg->max_batch * kRing, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(RPIV_ERR_OOM, "pinned pointer ring allocation failed");
+    }
+    for (int i = 0; i < kRing; ++i)
+        if ((e = cudaEventCreateWithFlags(&h->ring_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+            return cleanup(RPIV_ERR_CUDA, "event creation failed");
+    if ((e = cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cleanup(RPIV_ERR_CUDA, "event creation failed");
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup(RPIV_ERR_CUDA, "stream creation failed");
+    *out = h;
+    g_err.clear();
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_grid_shape(const rpiv_handle *h, int *nx, int *ny)
+{
+    if (!h || !nx || !ny) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    *nx = h->stages.back().nx;
+    *ny = h->stages.back().ny;
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_workspace_bytes(const rpiv_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    *bytes = h->ws_bytes + sizeof(PairIO) * h->cfg.max_batch + h->adj_bytes;
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, const void *const *img_b,
+                               size_t pitch_bytes, const float *const *pred_u, const float *const *pred_v,
+                               float *const *u, float *const *v, float *const *vort, uint8_t *const *mask,
+                               void *cuda_stream)
+{
+    if (!h) return fail(RPIV_ERR_INVALID_ARG, "handle is NULL");
+    if (n < 1 || n > h->cfg.max_batch)
+        return fail(RPIV_ERR_INVALID_ARG, "n = " + std::to_string(n) + " outside [1, max_batch = " +
+                                              std::to_string(h->cfg.max_batch) + "]");
+    if (!img_a || !img_b || !u || !v) return fail(RPIV_ERR_INVALID_ARG, "img_a, img_b, u and v must be non-NULL");
+    const size_t bpp = h->cfg.fmt == RPIV_U8 ? 1 : 2;
+    if (pitch_bytes < (size_t)h->cfg.width * bpp || pitch_bytes % bpp)
+        return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes smaller than width * bytes per pixel or misaligned");
+    if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
+    bool any_pred = false, any_nopred = false;
+    for (int i = 0; i < n; ++i) {
+        if (!img_a[i] || !img_b[i] || !u[i] || !v[i])
+            return fail(RPIV_ERR_INVALID_ARG, "NULL image or output pointer for pair " + std::to_string(i));
+        const bool hp = pred_u && pred_u[i];
+        if (pred_u && ((pred_u[i] == nullptr) != (pred_v[i] == nullptr)))
+            return fail(RPIV_ERR_INVALID_ARG, "pred_u/pred_v of pair " + std::to_string(i) + ": both or neither");
+        if (hp) any_pred = true;
+        else any_nopred = true;
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // pointer table for this call, staged in a pinned ring slot
+    const int slot = h->ring_pos;
+    h->ring_pos = (h->ring_pos + 1) % kRing;
+    if (h->ring_used[slot]) CK(cudaEventSynchronize(h->ring_ev[slot]), "pointer ring wait");
+    PairIO *tabh = h->ring + (size_t)slot * h->cfg.max_batch;
+    for (int i = 0; i < n; ++i) {
+        tabh[i].a = img_a[i];
+        tabh[i].b = img_b[i];
+        tabh[i].pred_u = pred_u ? pred_u[i] : nullptr;
+        tabh[i].pred_v = pred_v ? pred_v[i] : nullptr;
+        tabh[i].u = u[i];
+        tabh[i].v = v[i];
+        tabh[i].vort = vort ? vort[i] : nullptr;
+        tabh[i].mask = mask ? mask[i] : nullptr;
+    }
+    // one call at a time on the device per handle (shared workspace)
+    if (h->done_recorded) CK(cudaStreamWaitEvent(st, h->done_ev, 0), "ordering wait");
+    CK(cudaMemcpyAsync(h->io_dev, tabh, sizeof(PairIO) * n, cudaMemcpyHostToDevice, st), "pointer table copy");
+    CK(cudaEventRecord(h->ring_ev[slot], st), "event record");
+    h->ring_used[slot] = true;
+    // launch sequence: captured once per (n, predictor pattern, pitch), then replayed
+    char keybuf[96];
+    std::snprintf(keybuf, sizeof(keybuf), "%d/%d/%d/%zu", n, (int)any_pred, (int)any_nopred, pitch_bytes);
+    const std::string key(keybuf);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        // first use of this shape: run eagerly, then capture the same sequence
+        // on the handle's private stream for later replays
+        rpiv_status rs = enqueue_schedule(h, n, pitch_bytes, any_pred, any_nopred, st);
+        if (rs != RPIV_OK) return rs;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamSynchronize(st), "first-run synchronise");
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        rs = enqueue_schedule(h, n, pitch_bytes, any_pred, any_nopred, h->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (rs != RPIV_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rs;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+        h->graphs[key] = exec;
+    } else {
+        CK(cudaGraphLaunch(it->second, st), "graph launch");
+    }
+    CK(cudaEventRecord(h->done_ev, st), "event record");
+    h->done_recorded = true;
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_process_pair(rpiv_handle *h, const void *img_a, const void *img_b, size_t pitch_bytes,
+                              const float *pred_u, const float *pred_v, float *u, float *v, float *vort,
+                              uint8_t *mask, void *cuda_stream)
+{
+    if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
+    const void *a[1] = {img_a}, *b[1] = {img_b};
+    const float *pu[1] = {pred_u}, *pv[1] = {pred_v};
+    float *uu[1] = {u}, *vv[1] = {v}, *oo[1] = {vort};
+    uint8_t *mm[1] = {mask};
+    return rpiv_process_batch(h, 1, a, b, pitch_bytes, pred_u ? pu : nullptr, pred_v ? pv : nullptr, uu, vv, oo, mm,
+                              cuda_stream);
+}
+
+rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, size_t pitch_bytes, const float *u,
+                          const float *v, float grad_score, float *grad_u, float *grad_v, float *score_out,
+                          void *cuda_stream)
+{
+    if (!h || !img_a || !img_b || !u || !v) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if ((grad_u == nullptr) != (grad_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "grad_u and grad_v: both or neither");
+    const size_t bpp = h->cfg.fmt == RPIV_U8 ? 1 : 2;
+    if (pitch_bytes < (size_t)h->cfg.width * bpp || pitch_bytes % bpp)
+        return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes smaller than width * bytes per pixel or misaligned");
+    DeviceGuard dg(h->device);
+    const StageDef &d = h->stages[h->cfg.predictor_levels];  // first full-resolution pass grid
+    const size_t need = adjoint_workspace_bytes(d.W, d.H, d.nx, d.ny);
+    if (h->adj_bytes < need) {
+        // allocated on first use (not inside a stream capture)
+        if (h->adj_ws) {
+            cudaDeviceSynchronize();
+            cudaFree(h->adj_ws);
+            h->adj_ws = nullptr;
+            h->adj_bytes = 0;
+        }
+        if (cudaMalloc(&h->adj_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RPIV_ERR_OOM, "adjoint workspace allocation failed");
+        }
+        h->adj_bytes = need;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (h->done_recorded) CK(cudaStreamWaitEvent(st, h->done_ev, 0), "ordering wait");
+    AdjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.W = d.W;
+    a.H = d.H;
+    a.fmt = h->cfg.fmt == RPIV_U8 ? PIX_U8 : PIX_U16;
+    a.pitch = (long long)pitch_bytes;
+    a.img_a = ptr_direct(img_a, 0);
+    a.img_b = ptr_direct(img_b, 0);
+    a.w = d.w;
+    a.s = d.s;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.u = u;
+    a.v = v;
+    a.win_stats = reinterpret_cast<float *>(h->adj_ws);
+    a.pix_g = a.win_stats + up(8ull * d.nx * d.ny, 64);
+    a.grad_scale = grad_score;
+    a.grad_u = grad_u;
+    a.grad_v = grad_v;
+    a.score_out = score_out;
+    CK(launch_adjoint(a, st), "adjoint launch");
+    CK(cudaEventRecord(h->done_ev, st), "event record");
+    h->done_recorded = true;
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms)
+{
+    if (!h) return fail(RPIV_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->done_recorded) return RPIV_OK;
+    DeviceGuard dg(h->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(h->done_ev);
+        if (e == cudaSuccess) return RPIV_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "event query");
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if (ms.count() >= timeout_ms) return fail(RPIV_ERR_TIMEOUT, "work did not finish within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+rpiv_status rpiv_destroy(rpiv_handle *h)
+{
+    if (!h) return RPIV_OK;
+    {
+        DeviceGuard dg(h->device);
+        if (h->done_ev && h->done_recorded) cudaEventSynchronize(h->done_ev);
+        for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        for (int i = 0; i < kRing; ++i)
+            if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
+        if (h->done_ev) cudaEventDestroy(h->done_ev);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        if (h->ws) cudaFree(h->ws);
+        if (h->io_dev) cudaFree(h->io_dev);
+        if (h->ring) cudaFreeHost(h->ring);
+        if (h->adj_ws) cudaFree(h->adj_ws);
+        cudaGetLastError();
+    }
+    delete h;
+    return RPIV_OK;
+}
+
+// -------------------------------------------------------- stage entries --
+
+rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int width,
+                                 int height, int window, int step, int radius, rpiv_precision precision,
+                                 rpiv_deform deform_mode, const float *pred_u, const float *pred_v, float *u,
+                                 float *v, int32_t *info, void *cuda_stream)
+{
+    if (!img_a || !img_b || !u || !v || !info) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
+    if (fmt != 0 && fmt != RPIV_U8 && fmt != RPIV_U16) return fail(RPIV_ERR_INVALID_ARG, "fmt");
+    if (window < 2 || step < 1 || radius < 0 || radius > RPIV_MAX_RADIUS)
+        return fail(RPIV_ERR_INVALID_ARG, "window, step or radius out of range");
+    if (width < window + 2 * (radius + 1) || height < window + 2 * (radius + 1))
+        return fail(RPIV_ERR_INVALID_ARG, "image smaller than window + 2 (radius + 1)");
+    const int bpp = fmt == RPIV_U8 ? 1 : (fmt == RPIV_U16 ? 2 : 4);
+    if (pitch_bytes < (size_t)width * bpp || pitch_bytes % bpp) return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes");
+    if (precision != RPIV_FP32 && precision != RPIV_BF16 && precision != RPIV_FP16)
+        return fail(RPIV_ERR_INVALID_ARG, "precision");
+    const int nx = grid_n(width, window, step), ny = grid_n(height, window, step);
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.prec = radius == 0 ? PREC_FP32 : prec_of(precision);
+    if (!pass_plan(window, step, radius, nx, ny, a.prec, &a.plan))
+        return fail(RPIV_ERR_UNSUPPORTED, "no kernel for this radius/precision/block size");
+    a.W = width;
+    a.H = height;
+    a.fmt = fmt == RPIV_U8 ? PIX_U8 : (fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
+    a.pitch = (long long)pitch_bytes;
+    a.img_a = ptr_direct(img_a, 0);
+    a.img_b = ptr_direct(img_b, 0);
+    a.w = window;
+    a.s = step;
+    a.R = radius;
+    a.nx = nx;
+    a.ny = ny;
+    a.deform = deform_mode == RPIV_DEFORM_CENTRAL ? 1 : 0;
+    a.pred_u = ptr_direct(pred_u, 0);
+    a.pred_v = ptr_direct(pred_v, 0);
+    a.out_u = ptr_direct(u, 0);
+    a.out_v = ptr_direct(v, 0);
+    a.out_info = ptr_direct(info, 0);
+    prepare_pass_kernels();
+    CK(launch_pass(a, 1, static_cast<cudaStream_t>(cuda_stream)), "correlation pass launch");
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_stage_validate(const float *u, const float *v, const int32_t *info, int nx, int ny, float threshold,
+                                float eps, int replace, float *u_out, float *v_out, uint8_t *mask, void *cuda_stream)
+{
+    if (!u || !v || !u_out || !v_out || nx < 1 || ny < 1) return fail(RPIV_ERR_INVALID_ARG, "null argument or empty grid");
+    if (u == u_out || v == v_out) return fail(RPIV_ERR_INVALID_ARG, "input and output must not alias");
+    UodArgs a;
+    a.u = ptr_direct(u, 0);
+    a.v = ptr_direct(v, 0);
+    a.info = ptr_direct(info, 0);
+    a.nx = nx;
+    a.ny = ny;
+    a.thr = threshold;
+    a.eps = eps;
+    a.replace = replace ? 1 : 0;
+    a.u_out = ptr_direct(u_out, 0);
+    a.v_out = ptr_direct(v_out, 0);
+    a.mask = ptr_direct(mask, 0);
+    CK(launch_uod(a, 1, static_cast<cudaStream_t>(cuda_stream)), "outlier test launch");
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_stage_interp(const float *su, const float *sv, int snx, int sny, int sw, int ss, float *du,
+                              float *dv, int dnx, int dny, int dw, int ds, int levels_up, void *cuda_stream)
+{
+    if (!su || !sv || !du || !dv || snx < 1 || sny < 1 || dnx < 1 || dny < 1 || ss < 1 || ds < 1 || levels_up < 0 ||
+        levels_up > 8)
+        return fail(RPIV_ERR_INVALID_ARG, "bad argument");
+    InterpArgs a;
+    a.su = ptr_direct(su, 0);
+    a.sv = ptr_direct(sv, 0);
+    a.snx = snx;
+    a.sny = sny;
+    a.sw = sw;
+    a.ss = ss;
+    a.du = ptr_direct(du, 0);
+    a.dv = ptr_direct(dv, 0);
+    a.dnx = dnx;
+    a.dny = dny;
+    a.dw = dw;
+    a.ds = ds;
+    a.levels_up = levels_up;
+    a.zero_if_null = 0;
+    CK(launch_interp(a, 1, static_cast<cudaStream_t>(cuda_stream)), "interpolation launch");
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_stage_vorticity(const float *u, const float *v, int nx, int ny, int step, float *vort,
+                                 void *cuda_stream)
+{
+    if (!u || !v || !vort || nx < 1 || ny < 1 || step < 1) return fail(RPIV_ERR_INVALID_ARG, "bad argument");
+    VortArgs a;
+    a.u = ptr_direct(u, 0);
+    a.v = ptr_direct(v, 0);
+    a.out = ptr_direct(vort, 0);
+    a.nx = nx;
+    a.ny = ny;
+    a.s = step;
+    CK(launch_vort(a, 1, static_cast<cudaStream_t>(cuda_stream)), "vorticity launch");
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_stage_downsample(const void *img, size_t pitch_bytes, int fmt, int width, int height, float *out,
+                                  void *cuda_stream)
+{
+    if (!img || !out || width < 2 || height < 2) return fail(RPIV_ERR_INVALID_ARG, "bad argument");
+    if (fmt != 0 && fmt != RPIV_U8 && fmt != RPIV_U16) return fail(RPIV_ERR_INVALID_ARG, "fmt");
+    const int bpp = fmt == RPIV_U8 ? 1 : (fmt == RPIV_U16 ? 2 : 4);
+    if (pitch_bytes < (size_t)width * bpp) return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes");
+    DownArgs a;
+    a.src = ptr_direct(img, 0);
+    a.fmt = fmt == RPIV_U8 ? PIX_U8 : (fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
+    a.pitch = (long long)pitch_bytes;
+    a.W = width;
+    a.H = height;
+    a.dst = ptr_direct(out, 0);
+    CK(launch_down(a, 1, static_cast<cudaStream_t>(cuda_stream)), "downsample launch");
+    return RPIV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Internal interfaces between the host engine (engine.cpp, capi.cpp) and the
+// CUDA kernels (k_*.cu).  Not part of the public ABI (see include/rpiv.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace rpiv {
+
+enum PixFmt : int { PIX_F32 = 0, PIX_U8 = 1, PIX_U16 = 2 };
+enum Prec : int { PREC_FP32 = 0, PREC_BF16 = 1, PREC_FP16 = 2 };
+
+// Per-pair pointers of one batch call, mirrored into device memory.
+struct PairIO {
+    const void *a;
+    const void *b;
+    const float *pred_u;
+    const float *pred_v;
+    float *u;
+    float *v;
+    float *vort;
+    uint8_t *mask;
+};
+
+// A per-pair pointer: either direct (base + pair * stride) or read from a
+// device table (entry at base + pair * stride holds the pointer).
+struct PtrRef {
+    const char *base;
+    long long stride;
+    int indirect;
+};
+
+__host__ __device__ inline PtrRef ptr_direct(const void *p, long long stride)
+{
+    PtrRef r;
+    r.base = static_cast<const char *>(p);
+    r.stride = stride;
+    r.indirect = 0;
+    return r;
+}
+
+__host__ __device__ inline PtrRef ptr_table(const void *entry0, long long stride)
+{
+    PtrRef r;
+    r.base = static_cast<const char *>(entry0);
+    r.stride = stride;
+    r.indirect = 1;
+    return r;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ const void *resolve(const PtrRef &r, int pair)
+{
+    if (r.base == nullptr) return nullptr;
+    const char *p = r.base + (long long)pair * r.stride;
+    if (r.indirect) return *reinterpret_cast<const void *const *>(p);
+    return p;
+}
+#endif
+
+// ------------------------------------------------------------ pass kernel --
+
+struct PassPlan {
+    // tiling
+    int TX, TY, tiles_x, tiles_y, threads;
+    int G;    // block size of the block-decomposed correlation (= gcd(w, s))
+    int RGx;  // partial planes per block
+    // shared-memory layout (byte offsets) for a full tile
+    int smem_bytes;
+    int off_nodes, node_cap;     // predictor nodes (u then v), node_cap floats each
+    int off_tabs;                // per-column / per-row grid weights
+    int off_a, a_pitch;          // A - mu_T region, floats
+    int off_b, b_pitch, padl;    // B' - mu_T region, floats; logical column 0 at padl - (R+1)
+    int off_h, h_pitch;          // H1 then H2 (row box sums), floats
+    int off_v;                   // V1 then V2 (window box sums), floats
+    int off_p;                   // block partial planes (aliases H)
+    int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
+    int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path), elements
+    int off_scr;                 // TC epilogue scratch
+    int off_stats;               // per-window mean / energy of A
+    int off_red;                 // reduction scratch
+    int max_windows, max_blocks;
+};
+
+struct PassArgs {
+    int W, H, fmt;
+    long long pitch;       // bytes between image rows
+    PtrRef img_a, img_b;
+    int w, s, R, nx, ny;
+    int deform;            // 0: frame B only, 1: central
+    int prec;
+    PtrRef pred_u, pred_v; // predictor on this grid (base null: zero predictor)
+    PtrRef out_u, out_v;   // raw field
+    PtrRef out_info;       // int32: bit0 valid, bits 8..15 ky, 16..23 kx
+    PassPlan plan;
+};
+
+// Returns false if (w, s, R, prec) is not supported by a compiled kernel.
+bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan);
+cudaError_t launch_pass(const PassArgs &args, int n_pairs, cudaStream_t st);
+bool pass_supported(int R, int prec);
+
+// ------------------------------------------------------------ grid kernels --
+
+struct UodArgs {
+    PtrRef u, v, info;         // info may have null base (all valid)
+    int nx, ny;
+    float thr, eps;
+    int replace;
+    PtrRef u_out, v_out, mask; // mask may have null base per pair
+};
+cudaError_t launch_uod(const UodArgs &a, int n_pairs, cudaStream_t st);
+
+struct InterpArgs {
+    PtrRef su, sv;
+    int snx, sny, sw, ss;
+    PtrRef du, dv;
+    int dnx, dny, dw, ds, levels_up;
+    int zero_if_null;  // a pair whose source is null: write zeros (1) or leave the destination (0)
+};
+cudaError_t launch_interp(const InterpArgs &a, int n_pairs, cudaStream_t st);
+
+struct VortArgs {
+    PtrRef u, v, out;
+    int nx, ny, s;
+};
+cudaError_t launch_vort(const VortArgs &a, int n_pairs, cudaStream_t st);
+
+struct DownArgs {
+    PtrRef src;
+    int fmt;
+    long long pitch;   // bytes
+    int W, H;          // source size
+    PtrRef dst;        // float, floor(W/2) x floor(H/2), dense
+};
+cudaError_t launch_down(const DownArgs &a, int n_pairs, cudaStream_t st);
+
+
+// ---------------------------------------------------------------- adjoint --
+
+struct AdjArgs {
+    int W, H, fmt;
+    long long pitch;
+    PtrRef img_a, img_b;
+    int w, s, nx, ny;
+    const float *u, *v;    // field on the grid
+    float *win_stats;      // workspace: 8 floats per window
+    float *pix_g;          // workspace: 2 floats per pixel (dS/dX, dS/dY at the pixel)
+    float *score_part;     // workspace: one float per window row
+    float grad_scale;
+    float *grad_u, *grad_v, *score_out;
+};
+size_t adjoint_workspace_bytes(int W, int H, int nx, int ny);
+cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t st);
+
+}  // namespace rpiv
