@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Throughput and latency of the PIV correction path on GB300.
+
+Workload: 1024 x 1024 12-bit (uint16) synthetic particle pairs, 0.03 ppp,
+d_p U(2, 4) px, 10 % out-of-plane loss, uniform 12 px + shear layer + Lamb-Oseen
+vortex; 2-level correlation pyramid, then passes of 64 -> 32 -> 16 px windows at
+50 % overlap with a +-4 px search (127 x 127 vectors per pair).  One step = one
+batch of 64 pairs through the whole path (pyramid, deformation, correlation,
+peak, Gaussian fit, outlier test, interpolation, vorticity), inputs resident
+in device memory (256 MiB per step, larger than L2).
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1 MP PIV pairs/s and p99 latency, BF16 vs FP32 path at ≤0.01 px error vs oracle"
+N_DISTINCT = 8          # distinct synthetic pairs, replicated to fill a batch
+BATCH = 64
+WORKLOAD = ("paper_1mp_u16: 1024x1024 uint16 (12-bit) pair, 0.03 ppp, d_p U(2,4), 10% particle loss, "
+            "uniform 12 px + tanh shear + Lamb-Oseen; 2-level pyramid, passes 64->32->16 px, 50% overlap, "
+            "search +-4; 127x127 vectors")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=BATCH)
+    p.add_argument("--precisions", default="fp32,bf16,fp16")
+    p.add_argument("--headline", default="bf16")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--latency-requests", type=int, default=200)
+    p.add_argument("--mode", default="full", choices=["full", "ncu"],
+                   help="ncu: one warm-up step and one step of the headline path, nothing else (profiler runs)")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def _oracle_pair(seed: int):
+    """Render one pair and run the FP64 oracle on it; returns timing and field."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from synth import workloads as wl
+    w = wl.paper_1mp(seed=seed)
+    A, B = w.render()
+    sc = w.schedule
+    t0 = time.perf_counter()
+    r = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels)
+    dt = time.perf_counter() - t0
+    return seed, dt, r.u, r.v
+
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_round(pool, seeds):
+    """Runs the oracle on one pair per worker; the round lasts as long as its
+    slowest pair (rendering and process overhead excluded)."""
+    res = pool.map(_oracle_pair, seeds, chunksize=1)
+    return max(r[1] for r in res), res
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    synth.build()
+    cores = _host_cores()
+    per_step = cores
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range(args.warmup):
+            oracle_round(pool, [1002 + k for k in range(per_step)])
+        times = []
+        for _ in range(args.steps):
+            dt, _ = oracle_round(pool, [1002 + k for k in range(per_step)])
+            times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} pairs per step (one per core), {args.steps} steps"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.th is not None:
+            self.th.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- ours --
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = _host_cores()
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cores)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_17987_gb300 as rp
+    from synth import workloads as wl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    B = args.batch
+    seeds = [1002 + 100 * rank + k for k in range(N_DISTINCT)]
+    pairs = [wl.paper_1mp(seed=s).render() for s in seeds]
+    sched = wl.paper_1mp().schedule
+    H, W = pairs[0][0].shape
+    a_dev = [rp.to_device(pairs[i % N_DISTINCT][0], dev) for i in range(B)]
+    b_dev = [rp.to_device(pairs[i % N_DISTINCT][1], dev) for i in range(B)]
+    in_bytes = sum(t.numel() * t.element_size() for t in a_dev + b_dev)
+
+    if args.mode == "ncu":
+        cfg = rp.Config.from_schedule(W, H, sched, bit_depth=12, precision=args.headline, max_batch=B)
+        eng = rp.Engine(cfg, device=local)
+        outs = eng.empty_outputs(B)
+        for _ in range(2):
+            eng.process_batch(a_dev, b_dev, outs=outs)
+        torch.cuda.synchronize()
+        eng.close()
+        if pool is not None:
+            pool.close()
+        print(json.dumps({"mode": "ncu", "precision": args.headline, "batch": B, "steps": 2}))
+        return 0
+
+    precs = [p.strip() for p in args.precisions.split(",") if p.strip()]
+    if args.headline not in precs:
+        precs.append(args.headline)
+    paths = {}
+    traces = {}
+    fields = {}
+    clocks = None
+    for prec in precs:
+        cfg = rp.Config.from_schedule(W, H, sched, bit_depth=12, precision=prec, max_batch=B)
+        eng = rp.Engine(cfg, device=local)
+        outs = eng.empty_outputs(B)
+        for _ in range(args.warmup):
+            eng.process_batch(a_dev, b_dev, outs=outs)
+        barrier()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as cs:
+            barrier()
+            e0.record(st)
+            for _ in range(args.steps):
+                eng.process_batch(a_dev, b_dev, outs=outs)
+            e1.record(st)
+            barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        if prec == args.headline:
+            clocks = cs.summary()
+        fields[prec] = (outs[0][0].cpu().numpy(), outs[1][0].cpu().numpy())
+        # stage trace (eager launches bracketed by events, same stream)
+        eng.trace(True)
+        for _ in range(3):
+            eng.process_batch(a_dev, b_dev, outs=outs)
+        recs = eng.trace_read()
+        eng.trace(False)
+        traces[prec] = recs
+        paths[prec] = {"pairs_per_s": world * B * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
+                       "pass_ms_per_launch": {r["name"]: round(r["total_ms"] / r["launches"], 4)
+                                              for r in recs if r["name"].startswith("pass/")}}
+        eng.close()
+        del outs
+        torch.cuda.empty_cache()
+
+    head = args.headline
+    value = paths[head]["pairs_per_s"]
+
+    # ---- end to end through the public API with pinned host buffers
+    cfg = rp.Config.from_schedule(W, H, sched, bit_depth=12, precision=head, max_batch=B)
+    eng = rp.Engine(cfg, device=local)
+    a_host = [rp.to_device(pairs[i % N_DISTINCT][0], pin=True) for i in range(B)]
+    b_host = [rp.to_device(pairs[i % N_DISTINCT][1], pin=True) for i in range(B)]
+    a_in = [torch.empty_like(t, device=dev) for t in a_host]
+    b_in = [torch.empty_like(t, device=dev) for t in b_host]
+    outs = eng.empty_outputs(B)
+    host_outs = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+    out_bytes = sum(o.numel() * o.element_size() for o in outs)
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        for i in range(B):
+            a_in[i].copy_(a_host[i], non_blocking=True)
+            b_in[i].copy_(b_host[i], non_blocking=True)
+        eng.process_batch(a_in, b_in, outs=outs)
+        for o, ho in zip(outs, host_outs):
+            ho.copy_(o, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * B * e2e_steps / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": in_bytes,
+           "d2h_bytes_per_step": out_bytes}
+    eng.close()
+
+    # ---- single-pair latency (request = host pair in, field out)
+    cfg1 = rp.Config.from_schedule(W, H, sched, bit_depth=12, precision=head, max_batch=1)
+    eng1 = rp.Engine(cfg1, device=local)
+    o1 = eng1.empty_outputs(1)
+    h1 = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in o1]
+    lat = []
+    for k in range(args.latency_requests + 5):
+        t0 = time.perf_counter()
+        a_in[0].copy_(a_host[k % N_DISTINCT], non_blocking=True)
+        b_in[0].copy_(b_host[k % N_DISTINCT], non_blocking=True)
+        eng1.process_pair(a_in[0], b_in[0], out=o1)
+        for o, ho in zip(o1, h1):
+            ho.copy_(o, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if k >= 5:
+            lat.append(1000.0 * (time.perf_counter() - t0))
+    eng1.close()
+    lat.sort()
+    latency = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+               "requests": len(lat), "batch": 1, "what": "pinned host pair -> device -> full path -> field on host"}
+
+    # ---- roofline of the dominant kernel (traced launches of the headline path)
+    recs = traces[head]
+    passes = [r for r in recs if r["name"].startswith("pass/")]
+    dom = max(passes, key=lambda r: r["total_ms"])
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    region = ((dom["nx"] - 1) * dom["step"] + dom["window"]) * ((dom["ny"] - 1) * dom["step"] + dom["window"])
+    plane_flops = 2.0 * region * (2 * dom["radius"] + 1) ** 2 * dom["pairs"]
+    direct_flops = 2.0 * dom["nx"] * dom["ny"] * dom["window"] ** 2 * (2 * dom["radius"] + 1) ** 2 * dom["pairs"]
+    achieved = plane_flops / (per_launch_ms / 1000.0) / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    if head == "fp32":
+        bound, peak, peak_src = "alu", fp32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    else:
+        bound = "tensor"
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak_src = "measured (MEASURED_PEAKS.json bf16_tflops_sustained)" if peaks else "fallback"
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        key = f"{head}/{dom['name']}"
+        ent = tr.get(key)
+        src_hash = _kernel_source_hash()
+        if ent and ent.get("source_hash") == src_hash:
+            traffic = ent["bytes_per_pair"] * dom["pairs"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": f"pass_kernel {dom['name']} (w={dom['window']}, s={dom['step']}, "
+                f"r={dom['radius']}, {dom['pairs']} pairs/launch)", "peak_source": peak_src,
+                "per_launch_ms": per_launch_ms, "algorithmic_flops_per_launch": plane_flops,
+                "direct_equivalent_flops_per_launch": direct_flops}
+    stage_ms = {r["name"]: r["total_ms"] / r["launches"] for r in recs}
+    launches_per_step = sum(r["launches"] for r in recs) / 3.0
+
+    # ---- CPU baseline and accuracy against the FP64 oracle
+    cpu = None
+    accuracy = {}
+    if pool is not None:
+        sample_seeds = [1002 + k for k in range(cores)]
+        dt, res = oracle_round(pool, sample_seeds)
+        pool.close()
+        cpu = {"value": len(sample_seeds) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(sample_seeds)} pairs of the workload, one per core, FP64 oracle, "
+                         f"{dt:.1f} s wall"}
+        ref = {r[0]: r for r in res}
+        if seeds[0] in ref:
+            ru, rv = ref[seeds[0]][2], ref[seeds[0]][3]
+            for prec, (u, v) in fields.items():
+                err = np.maximum(np.abs(u - ru), np.abs(v - rv))
+                accuracy[prec] = {"p99_px": float(np.percentile(err, 99)), "max_px": float(err.max()),
+                                  "within_1e-3": float(np.mean(err <= 1e-3))}
+    for prec in paths:
+        if prec in accuracy:
+            paths[prec]["err_vs_oracle"] = accuracy[prec]
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": paths[head]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_pairs_per_gpu": B, "precision": head,
+                       "l2": f"inputs {in_bytes / 2**20:.0f} MiB per step > 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "paths": paths, "latency": latency, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clocks, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "stage_ms_per_launch": stage_ms,
+            "vectors_per_s": value * 127 * 127,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pass_impl.cuh", "k_pass_fp32.cu", "k_pass_bf16.cu", "k_pass_fp16.cu", "pass_plan.cpp"):
+        with open(os.path.join(ROOT, "paper_2504_17987_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -161,6 +161,26 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
  * timeout_ms milliseconds (host watchdog).  RPIV_ERR_TIMEOUT if it has not.  */
 rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms);
 
+/* Stage tracing.  While enabled, rpiv_process_batch/rpiv_process_pair run
+ * their launch sequence eagerly (no graph replay) and bracket every kernel
+ * launch with CUDA events on the caller's stream.  rpiv_trace_read
+ * synchronises the handle's work and returns one record per traced stage
+ * (aggregated over calls since the last read, then cleared): name (e.g.
+ * "pass/p2" for full-resolution pass 2, "pass/L1" for pyramid level 1,
+ * "uod/p2", "interp/p2", "down/L1", "vort"), launches, total milliseconds,
+ * and the stage geometry (image size, window, step, radius, grid, pairs per
+ * launch) from which throughput is derived.  cap = capacity of out; *n = number
+ * of records (may exceed cap; only cap are written).                         */
+typedef struct {
+    char name[24];
+    int launches;
+    float total_ms;
+    int width, height, window, step, radius, nx, ny, pairs;
+} rpiv_trace_record;
+
+rpiv_status rpiv_trace_enable(rpiv_handle *h, int enable);
+rpiv_status rpiv_trace_read(rpiv_handle *h, rpiv_trace_record *out, int cap, int *n);
+
 /* Synchronises and frees everything the handle owns.  NULL is a no-op.      */
 rpiv_status rpiv_destroy(rpiv_handle *h);
 
@@ -178,16 +198,25 @@ const char *rpiv_last_error(void);
 /* One correlation pass (paper Sec. 2: warp, correlation coefficient around
  * the peak, Gaussian sub-pixel fit) on the grid (w, step) of a W x H image.
  *   fmt        RPIV_U8, RPIV_U16, or 0 for float32 images (pyramid levels).
- *   pred_u/v   predictor on this grid's nodes (device, ny x nx float).
+ *   pred_u/v   predictor on this grid's nodes (device, ny x nx float), or
+ *              both NULL for a zero predictor.
  *   u, v       raw (pre-validation) result, ny x nx float.
  *   info       ny x nx int32: bit 0 valid window, bits 8..15 the integer peak
  *              ky and bits 16..23 kx as int8.
- * Errors: INVALID_ARG (sizes, nulls, radius), UNSUPPORTED (precision not
- * built for this radius), CUDA.                                              */
+ *   scratch    caller-owned device buffer of at least the size returned by
+ *              rpiv_stage_correlate_scratch_bytes (the warped frame(s)); it
+ *              must not be in use by other work on the device.
+ * Errors: INVALID_ARG (sizes, nulls, radius, small scratch), UNSUPPORTED
+ * (precision not built for this radius or step), CUDA.                      */
 rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int width,
                                  int height, int window, int step, int radius, rpiv_precision precision,
                                  rpiv_deform deform_mode, const float *pred_u, const float *pred_v, float *u,
-                                 float *v, int32_t *info, void *cuda_stream);
+                                 float *v, int32_t *info, void *scratch, size_t scratch_bytes, void *cuda_stream);
+
+/* Scratch bytes rpiv_stage_correlate needs for a W x H image and radius r:
+ * one float image grown by r + 1 pixels per side (two for the central warp). */
+rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius, rpiv_deform deform_mode,
+                                               size_t *bytes);
 
 /* Normalised median test + median replacement (paper Sec. 2, Westerweel &
  * Scarano 2005) on an nx x ny field; info (nullable) marks invalid windows

@@ -23,16 +23,23 @@ RPIV_DEFORM_B, RPIV_DEFORM_CENTRAL = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY", 7: "NO_DEVICE"}
 PRECISIONS = {"fp32": RPIV_FP32, "bf16": RPIV_BF16, "fp16": RPIV_FP16}
 
-EXPORTED = ["rpiv_config_default", "rpiv_validate_config", "rpiv_create", "rpiv_grid_shape", "rpiv_workspace_bytes",
-            "rpiv_process_pair", "rpiv_process_batch", "rpiv_backward", "rpiv_wait", "rpiv_destroy",
-            "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_validate", "rpiv_stage_interp",
-            "rpiv_stage_vorticity", "rpiv_stage_downsample"]
+EXPORTED = sorted(["rpiv_config_default", "rpiv_validate_config", "rpiv_create", "rpiv_grid_shape",
+                   "rpiv_workspace_bytes", "rpiv_process_pair", "rpiv_process_batch", "rpiv_backward", "rpiv_wait",
+                   "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes", "rpiv_stage_validate",
+                   "rpiv_stage_interp", "rpiv_stage_vorticity", "rpiv_stage_downsample", "rpiv_trace_enable",
+                   "rpiv_trace_read"])
 
 
 class RpivError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"rpiv {STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class TraceRecord(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int), ("total_ms", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("window", ctypes.c_int), ("step", ctypes.c_int),
+                ("radius", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pairs", ctypes.c_int)]
 
 
 class _Config(ctypes.Structure):
@@ -71,11 +78,15 @@ def load(path: str = LIB_PATH):
     L.rpiv_backward.argtypes = [vp, vp, vp, sz, vp, vp, f32, vp, vp, vp, vp]
     L.rpiv_wait.argtypes = [vp, i32]
     L.rpiv_destroy.argtypes = [vp]
-    L.rpiv_stage_correlate.argtypes = [vp, vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.rpiv_stage_correlate.argtypes = [vp, vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, sz,
+                                       vp]
+    L.rpiv_stage_correlate_scratch_bytes.argtypes = [i32, i32, i32, i32, ctypes.POINTER(sz)]
     L.rpiv_stage_validate.argtypes = [vp, vp, vp, i32, i32, f32, f32, i32, vp, vp, vp, vp]
     L.rpiv_stage_interp.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp]
     L.rpiv_stage_vorticity.argtypes = [vp, vp, i32, i32, i32, vp, vp]
     L.rpiv_stage_downsample.argtypes = [vp, sz, i32, i32, i32, vp, vp]
+    L.rpiv_trace_enable.argtypes = [vp, i32]
+    L.rpiv_trace_read.argtypes = [vp, ctypes.POINTER(TraceRecord), i32, ctypes.POINTER(i32)]
     for name in EXPORTED:
         if name != "rpiv_last_error":
             getattr(L, name).restype = ctypes.c_int
@@ -265,6 +276,23 @@ class Engine:
                                     float(grad_score), _ptr(gu), _ptr(gv), _ptr(score), _stream(stream)))
         return score, gu, gv
 
+    def trace(self, enable: bool = True):
+        """Stage tracing: eager launches bracketed by CUDA events."""
+        _check(load().rpiv_trace_enable(self.handle, 1 if enable else 0))
+
+    def trace_read(self):
+        """Per-stage records since the last read (synchronises the handle's work)."""
+        cap = 64
+        recs = (TraceRecord * cap)()
+        n = ctypes.c_int()
+        _check(load().rpiv_trace_read(self.handle, recs, cap, ctypes.byref(n)))
+        out = []
+        for r in recs[:min(cap, n.value)]:
+            out.append(dict(name=r.name.decode(), launches=r.launches, total_ms=r.total_ms, width=r.width,
+                            height=r.height, window=r.window, step=r.step, radius=r.radius, nx=r.nx, ny=r.ny,
+                            pairs=r.pairs))
+        return out
+
     def wait(self, timeout_ms: int = 60000):
         _check(load().rpiv_wait(self.handle, int(timeout_ms)))
 
@@ -297,10 +325,13 @@ def stage_correlate(a, b, w: int, s: int, r: int, pred_u=None, pred_v=None, prec
     u = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     v = torch.empty_like(u)
     info = torch.empty((ny, nx), dtype=torch.int32, device=dev)
+    dm = RPIV_DEFORM_CENTRAL if deform == "central" else RPIV_DEFORM_B
+    nbytes = ctypes.c_size_t()
+    _check(load().rpiv_stage_correlate_scratch_bytes(W, H, r, dm, ctypes.byref(nbytes)))
+    scratch = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=dev)
     _check(load().rpiv_stage_correlate(_ptr(a), _ptr(b), a.stride(0) * a.element_size(), _fmt_code(a), W, H, w, s, r,
-                                       PRECISIONS[precision],
-                                       RPIV_DEFORM_CENTRAL if deform == "central" else RPIV_DEFORM_B,
-                                       _ptr(pred_u), _ptr(pred_v), _ptr(u), _ptr(v), _ptr(info), _stream(stream)))
+                                       PRECISIONS[precision], dm, _ptr(pred_u), _ptr(pred_v), _ptr(u), _ptr(v),
+                                       _ptr(info), _ptr(scratch), nbytes.value, _stream(stream)))
     return u, v, info
 
 

@@ -132,6 +132,8 @@ std::string check_config(const rpiv_config *c, std::vector<StageDef> *stages_out
                    std::to_string(d.W) + "x" + std::to_string(d.H) + " is smaller than window + 2 (radius + 1)";
         d.nx = grid_n(d.W, d.w, d.s);
         d.ny = grid_n(d.H, d.w, d.s);
+        if (!deform_nodes_fit(d.w, d.s, d.nx, d.ny))
+            return "step " + std::to_string(d.s) + " is too small for the deformation kernel (minimum 3)";
         // a zero radius has a one-point plane: the FP32 kernel serves every precision
         d.prec = d.R == 0 ? PREC_FP32 : prec_of(c->precision);
         if (!pass_plan(d.w, d.s, d.R, d.nx, d.ny, d.prec, &d.plan))
@@ -151,6 +153,9 @@ struct rpiv_handle {
     int device = 0;
     std::vector<StageDef> stages;
     size_t pyr_off[RPIV_MAX_LEVELS + 1][2] = {};  // per-pair offsets of pyramid A/B images (level >= 1)
+    size_t def_off[2] = {};                       // per-pair offsets of the warped frames B' (and A')
+    int def_margin = 0;
+    long long def_pitch = 0;                      // floats per row of a warped frame
     size_t pair_stride = 0;
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -165,6 +170,15 @@ struct rpiv_handle {
     std::map<std::string, cudaGraphExec_t> graphs;
     char *adj_ws = nullptr;
     size_t adj_bytes = 0;
+    // stage tracing
+    bool tracing = false;
+    struct TraceEv {
+        std::string name;
+        cudaEvent_t t0, t1;
+        rpiv_trace_record geom;
+    };
+    std::vector<TraceEv> trace_evs;
+    std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace {
@@ -182,6 +196,64 @@ struct DeviceGuard {
     }
 };
 
+cudaEvent_t pool_event(rpiv_handle *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch with events when tracing (never inside a capture).
+struct TraceScope {
+    rpiv_handle *h;
+    cudaStream_t st;
+    bool on;
+    rpiv_handle::TraceEv ev;
+    TraceScope(rpiv_handle *h_, cudaStream_t st_, const std::string &name, const rpiv_trace_record &g)
+        : h(h_), st(st_), on(h_->tracing)
+    {
+        if (!on) return;
+        ev.name = name;
+        ev.geom = g;
+        ev.t0 = pool_event(h);
+        ev.t1 = pool_event(h);
+        cudaEventRecord(ev.t0, st);
+    }
+    ~TraceScope()
+    {
+        if (!on) return;
+        cudaEventRecord(ev.t1, st);
+        h->trace_evs.push_back(ev);
+    }
+};
+
+rpiv_trace_record geom_of(int W, int H, int w, int s, int R, int nx, int ny, int n)
+{
+    rpiv_trace_record g;
+    std::memset(&g, 0, sizeof(g));
+    g.width = W;
+    g.height = H;
+    g.window = w;
+    g.step = s;
+    g.radius = R;
+    g.nx = nx;
+    g.ny = ny;
+    g.pairs = n;
+    return g;
+}
+
+std::string stage_tag(const rpiv_handle *h, const StageDef &d)
+{
+    if (d.level) return "L" + std::to_string(d.lvl);
+    const int p = (int)(&d - &h->stages[0]) - h->cfg.predictor_levels;
+    return "p" + std::to_string(p);
+}
+
 // The full schedule for n pairs whose pointers are in h->io_dev.
 rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred, bool any_nopred, cudaStream_t st)
 {
@@ -197,8 +269,36 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
     const bool run_pyr = L > 0 && any_nopred;
 
     auto run_pass = [&](const StageDef &d, PtrRef A, PtrRef B, int fmt, long long pch, bool pred) -> rpiv_status {
+        const size_t n1 = (size_t)d.nx * d.ny;
+        const bool central = c.deform_mode == RPIV_DEFORM_CENTRAL;
+        for (int which = central ? 0 : 1; which < 2; ++which) {
+            DeformArgs da;
+            std::memset(&da, 0, sizeof(da));
+            da.img = which ? B : A;
+            da.fmt = fmt;
+            da.pitch = pch;
+            da.W = d.W;
+            da.H = d.H;
+            da.pred_u = pred ? ws(d.off_pred) : ptr_direct(nullptr, 0);
+            da.pred_v = pred ? ws(d.off_pred + 4 * n1) : ptr_direct(nullptr, 0);
+            da.w = d.w;
+            da.s = d.s;
+            da.nx = d.nx;
+            da.ny = d.ny;
+            da.scale = central ? (which ? 0.5f : -0.5f) : 1.0f;
+            da.M = h->def_margin;
+            da.out = ws(h->def_off[which]);
+            da.out_pitch = h->def_pitch;
+            TraceScope ts(h, st, std::string(which ? "deform/" : "deformA/") + stage_tag(h, d),
+                          geom_of(d.W, d.H, d.w, d.s, d.R, d.nx, d.ny, n));
+            CK(launch_deform(da, n, st), "deformation launch");
+        }
         PassArgs a;
         std::memset(&a, 0, sizeof(a));
+        a.bdef = ws(h->def_off[1]);
+        a.adef = central ? ws(h->def_off[0]) : ptr_direct(nullptr, 0);
+        a.def_pitch = h->def_pitch;
+        a.def_margin = h->def_margin;
         a.W = d.W;
         a.H = d.H;
         a.fmt = fmt;
@@ -212,13 +312,13 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
         a.ny = d.ny;
         a.deform = c.deform_mode == RPIV_DEFORM_CENTRAL ? 1 : 0;
         a.prec = d.prec;
-        const size_t n1 = (size_t)d.nx * d.ny;
         a.pred_u = pred ? ws(d.off_pred) : ptr_direct(nullptr, 0);
         a.pred_v = pred ? ws(d.off_pred + 4 * n1) : ptr_direct(nullptr, 0);
         a.out_u = ws(d.off_raw);
         a.out_v = ws(d.off_raw + 4 * n1);
         a.out_info = ws(d.off_info);
         a.plan = d.plan;
+        TraceScope ts(h, st, "pass/" + stage_tag(h, d), geom_of(d.W, d.H, d.w, d.s, d.R, d.nx, d.ny, n));
         CK(launch_pass(a, n, st), "correlation pass launch");
         return RPIV_OK;
     };
@@ -242,6 +342,7 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
             u.v_out = ws(d.off_out + 4 * n1);
             u.mask = ws(d.off_mask);
         }
+        TraceScope ts(h, st, "uod/" + stage_tag(h, d), geom_of(d.W, d.H, d.w, d.s, d.R, d.nx, d.ny, n));
         CK(launch_uod(u, n, st), "outlier test launch");
         return RPIV_OK;
     };
@@ -263,6 +364,8 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
         ia.ds = dst.s;
         ia.levels_up = lv_up;
         ia.zero_if_null = zero_if_null;
+        TraceScope ts(h, st, "interp/" + stage_tag(h, dst),
+                      geom_of(dst.W, dst.H, dst.w, dst.s, dst.R, dst.nx, dst.ny, n));
         CK(launch_interp(ia, n, st), "interpolation launch");
         return RPIV_OK;
     };
@@ -288,6 +391,7 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
                     d.H = prev.H;
                 }
                 d.dst = ws(h->pyr_off[l][ab]);
+                TraceScope ts(h, st, "down/L" + std::to_string(l), geom_of(d.W, d.H, 0, 0, 0, 0, 0, n));
                 CK(launch_down(d, n, st), "pyramid launch");
             }
         }
@@ -340,6 +444,7 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
     va.nx = fin.nx;
     va.ny = fin.ny;
     va.s = fin.s;
+    TraceScope ts(h, st, "vort", geom_of(fin.W, fin.H, fin.w, fin.s, fin.R, fin.nx, fin.ny, n));
     CK(launch_vort(va, n, st), "vorticity launch");
     return RPIV_OK;
 }
@@ -419,6 +524,15 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
             h->pyr_off[l][0] = take((size_t)W * H * 4);
             h->pyr_off[l][1] = take((size_t)W * H * 4);
         }
+    }
+    {
+        int M = 0;
+        for (auto &d : h->stages) M = std::max(M, d.R + 1);
+        h->def_margin = M;
+        h->def_pitch = (long long)up((size_t)cfg->width + 2 * M, 32);
+        const size_t bytes = (size_t)h->def_pitch * (cfg->height + 2 * M) * 4;
+        h->def_off[1] = take(bytes);
+        if (cfg->deform_mode == RPIV_DEFORM_CENTRAL) h->def_off[0] = take(bytes);
     }
     for (auto &d : h->stages) {
         const size_t n1 = (size_t)d.nx * d.ny;
@@ -527,7 +641,10 @@ rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, 
     std::snprintf(keybuf, sizeof(keybuf), "%d/%d/%d/%zu", n, (int)any_pred, (int)any_nopred, pitch_bytes);
     const std::string key(keybuf);
     auto it = h->graphs.find(key);
-    if (it == h->graphs.end()) {
+    if (h->tracing) {
+        rpiv_status rs = enqueue_schedule(h, n, pitch_bytes, any_pred, any_nopred, st);
+        if (rs != RPIV_OK) return rs;
+    } else if (it == h->graphs.end()) {
         // first use of this shape: run eagerly, then capture the same sequence
         // on the handle's private stream for later replays
         rpiv_status rs = enqueue_schedule(h, n, pitch_bytes, any_pred, any_nopred, st);
@@ -638,6 +755,44 @@ rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms)
     }
 }
 
+rpiv_status rpiv_trace_enable(rpiv_handle *h, int enable)
+{
+    if (!h) return fail(RPIV_ERR_INVALID_ARG, "handle is NULL");
+    h->tracing = enable != 0;
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_trace_read(rpiv_handle *h, rpiv_trace_record *out, int cap, int *n)
+{
+    if (!h || !n || (cap > 0 && !out)) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    DeviceGuard dg(h->device);
+    std::vector<rpiv_trace_record> recs;
+    std::map<std::string, size_t> index;
+    for (auto &t : h->trace_evs) {
+        CK(cudaEventSynchronize(t.t1), "trace synchronise");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, t.t0, t.t1), "trace elapsed time");
+        auto it = index.find(t.name);
+        if (it == index.end()) {
+            rpiv_trace_record r = t.geom;
+            std::snprintf(r.name, sizeof(r.name), "%s", t.name.c_str());
+            r.launches = 0;
+            r.total_ms = 0.f;
+            index[t.name] = recs.size();
+            recs.push_back(r);
+            it = index.find(t.name);
+        }
+        recs[it->second].launches += 1;
+        recs[it->second].total_ms += ms;
+        h->ev_pool.push_back(t.t0);
+        h->ev_pool.push_back(t.t1);
+    }
+    h->trace_evs.clear();
+    *n = (int)recs.size();
+    for (int i = 0; i < cap && i < (int)recs.size(); ++i) out[i] = recs[i];
+    return RPIV_OK;
+}
+
 rpiv_status rpiv_destroy(rpiv_handle *h)
 {
     if (!h) return RPIV_OK;
@@ -645,6 +800,11 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
         DeviceGuard dg(h->device);
         if (h->done_ev && h->done_recorded) cudaEventSynchronize(h->done_ev);
         for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        for (auto &t : h->trace_evs) {
+            cudaEventDestroy(t.t0);
+            cudaEventDestroy(t.t1);
+        }
+        for (auto e : h->ev_pool) cudaEventDestroy(e);
         for (int i = 0; i < kRing; ++i)
             if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
         if (h->done_ev) cudaEventDestroy(h->done_ev);
@@ -661,12 +821,31 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
 
 // -------------------------------------------------------- stage entries --
 
+static void stage_def_geom(int width, int height, int radius, long long *pitch, size_t *one)
+{
+    const int M = radius + 1;
+    *pitch = (long long)up((size_t)width + 2 * M, 32);
+    *one = (size_t)(*pitch) * (height + 2 * M) * 4;
+}
+
+rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius, rpiv_deform deform_mode,
+                                               size_t *bytes)
+{
+    if (!bytes || width < 1 || height < 1 || radius < 0 || radius > RPIV_MAX_RADIUS)
+        return fail(RPIV_ERR_INVALID_ARG, "bad argument");
+    long long pitch;
+    size_t one;
+    stage_def_geom(width, height, radius, &pitch, &one);
+    *bytes = up(one, 256) * (deform_mode == RPIV_DEFORM_CENTRAL ? 2 : 1);
+    return RPIV_OK;
+}
+
 rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int width,
                                  int height, int window, int step, int radius, rpiv_precision precision,
                                  rpiv_deform deform_mode, const float *pred_u, const float *pred_v, float *u,
-                                 float *v, int32_t *info, void *cuda_stream)
+                                 float *v, int32_t *info, void *scratch, size_t scratch_bytes, void *cuda_stream)
 {
-    if (!img_a || !img_b || !u || !v || !info) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if (!img_a || !img_b || !u || !v || !info || !scratch) return fail(RPIV_ERR_INVALID_ARG, "null argument");
     if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
     if (fmt != 0 && fmt != RPIV_U8 && fmt != RPIV_U16) return fail(RPIV_ERR_INVALID_ARG, "fmt");
     if (window < 2 || step < 1 || radius < 0 || radius > RPIV_MAX_RADIUS)
@@ -677,31 +856,68 @@ rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pi
     if (pitch_bytes < (size_t)width * bpp || pitch_bytes % bpp) return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes");
     if (precision != RPIV_FP32 && precision != RPIV_BF16 && precision != RPIV_FP16)
         return fail(RPIV_ERR_INVALID_ARG, "precision");
+    if (deform_mode != RPIV_DEFORM_B && deform_mode != RPIV_DEFORM_CENTRAL)
+        return fail(RPIV_ERR_INVALID_ARG, "deform_mode");
+    size_t need = 0;
+    rpiv_stage_correlate_scratch_bytes(width, height, radius, deform_mode, &need);
+    if (scratch_bytes < need) return fail(RPIV_ERR_INVALID_ARG, "scratch smaller than rpiv_stage_correlate_scratch_bytes");
     const int nx = grid_n(width, window, step), ny = grid_n(height, window, step);
+    if (!deform_nodes_fit(window, step, nx, ny)) return fail(RPIV_ERR_UNSUPPORTED, "step too small (minimum 3)");
     PassArgs a;
     std::memset(&a, 0, sizeof(a));
     a.prec = radius == 0 ? PREC_FP32 : prec_of(precision);
     if (!pass_plan(window, step, radius, nx, ny, a.prec, &a.plan))
         return fail(RPIV_ERR_UNSUPPORTED, "no kernel for this radius/precision/block size");
+    long long dpitch;
+    size_t one;
+    stage_def_geom(width, height, radius, &dpitch, &one);
+    char *bdef = static_cast<char *>(scratch);
+    char *adef = deform_mode == RPIV_DEFORM_CENTRAL ? bdef + up(one, 256) : nullptr;
+    const int pfmt = fmt == RPIV_U8 ? PIX_U8 : (fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    prepare_pass_kernels();
+    for (int which = adef ? 0 : 1; which < 2; ++which) {
+        DeformArgs da;
+        std::memset(&da, 0, sizeof(da));
+        da.img = ptr_direct(which ? img_b : img_a, 0);
+        da.fmt = pfmt;
+        da.pitch = (long long)pitch_bytes;
+        da.W = width;
+        da.H = height;
+        da.pred_u = ptr_direct(pred_u, 0);
+        da.pred_v = ptr_direct(pred_v, 0);
+        da.w = window;
+        da.s = step;
+        da.nx = nx;
+        da.ny = ny;
+        da.scale = adef ? (which ? 0.5f : -0.5f) : 1.0f;
+        da.M = radius + 1;
+        da.out = ptr_direct(which ? bdef : adef, 0);
+        da.out_pitch = dpitch;
+        CK(launch_deform(da, 1, st), "deformation launch");
+    }
     a.W = width;
     a.H = height;
-    a.fmt = fmt == RPIV_U8 ? PIX_U8 : (fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
+    a.fmt = pfmt;
     a.pitch = (long long)pitch_bytes;
     a.img_a = ptr_direct(img_a, 0);
     a.img_b = ptr_direct(img_b, 0);
+    a.bdef = ptr_direct(bdef, 0);
+    a.adef = ptr_direct(adef, 0);
+    a.def_pitch = dpitch;
+    a.def_margin = radius + 1;
     a.w = window;
     a.s = step;
     a.R = radius;
     a.nx = nx;
     a.ny = ny;
-    a.deform = deform_mode == RPIV_DEFORM_CENTRAL ? 1 : 0;
+    a.deform = adef ? 1 : 0;
     a.pred_u = ptr_direct(pred_u, 0);
     a.pred_v = ptr_direct(pred_v, 0);
     a.out_u = ptr_direct(u, 0);
     a.out_v = ptr_direct(v, 0);
     a.out_info = ptr_direct(info, 0);
-    prepare_pass_kernels();
-    CK(launch_pass(a, 1, static_cast<cudaStream_t>(cuda_stream)), "correlation pass launch");
+    CK(launch_pass(a, 1, st), "correlation pass launch");
     return RPIV_OK;
 }
 

@@ -1,27 +1,26 @@
-// Fused correlation pass: image deformation, zero-normalised correlation
-// plane over a +-R search, integer peak, FP32 5-point refit and three-point
-// Gaussian fit, for a tile of TX x TY interrogation windows per CTA
-// (paper Sec. 2: warp the pair by the predictor, correlation coefficients on
-// a stencil around the peak, Gaussian sub-pixel interpolation).
+// Fused correlation pass over a tile of TX x TY interrogation windows per
+// CTA (paper Sec. 2: correlation coefficients of the warped pair around the
+// peak, three-point Gaussian sub-pixel interpolation).  The warped frame B'
+// is produced beforehand by the deformation kernel (k_deform.cu).
 //
-// Layout of the work in one CTA (all staged in shared memory):
+// Work of one CTA, staged in shared memory:
 //   A region   A - mu_T over the union of the tile's windows (aw x ah)
-//   B' region  B(x + d(x)) - mu_T over the A region grown by R+1 on each side
-//   H, V       sliding box sums of B' and B'^2: V[r][c] is the sum over the
-//              w x w box with top-left (r, c), i.e. sum_x B'(x + s) of every
-//              window at every shift s in [-R-1, R+1]^2 by lookup
+//   B' region  B' - mu_T over the A region grown by R+1 on each side
+//   C, V       sliding box sums of B' and B'^2: V[r][c] is the sum over the
+//              w x w box with top-left logical B' pixel (r, c), i.e. the sums
+//              of every window at every shift in [-R-1, R+1]^2, by lookup
 //   P          block partial planes: the A region is cut into G x G blocks
 //              (G = gcd(w, s)); P_b(s) = sum_{x in b} A_c(x) B'_c(x + s).
 //              A window's numerator is the sum of its (w/G)^2 block planes
 //              minus mean(A_c) * sum B'_c(x + s); this regrouping is exact,
-//              and it computes each block once instead of once per
-//              overlapping window.
-//   The plane is formed either with FP32 FMAs on the CUDA cores, or with
-//   BF16/FP16 tensor-core MMAs (mma.sync m16n8k8, FP32 accumulate) whose
-//   accumulator tile D[i][j] (i = B' row, j = A row of an 8-row sub-block)
-//   holds shift sy = i - j - R on its diagonals.  The argmax is taken on the
-//   plane; the 5-point stencil for the Gaussian fit is evaluated in FP32
-//   (from the FP32 block planes, or directly on the TC path).
+//              and computes each block once instead of once per overlapping
+//              window.
+// The planes are formed with FP32 FMAs on the CUDA cores, or with BF16/FP16
+// tensor-core MMAs (mma.sync m16n8k8, FP32 accumulate) whose accumulator tile
+// D[i][j] (i = B' row, j = A row of an 8-row sub-block) carries shift
+// sy = i - j - R on its diagonals.  The argmax is taken on the plane; the
+// 5-point stencil of the Gaussian fit is evaluated in FP32 (from the FP32
+// planes, or by direct sums on the tensor-core path and for shifts R+1).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -42,22 +41,27 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Node index i0 (local to the grid) and weight t of node i0+1 for an image
-// position along one axis; outside the node hull the border node is used.
-__device__ __forceinline__ void axis_w(int pos, int n, float c0, int s, int &i0, float &t)
-{
-    if (n <= 1) {
-        i0 = 0;
-        t = 0.f;
-        return;
+// Row-major walk over a width-W region with a fixed stride and no division
+// per step: start at element `start`, advance by `stride` elements.
+struct Walk2D {
+    int x, y, sx, sy, W;
+    __device__ __forceinline__ Walk2D(int start, int stride, int W_) : W(W_)
+    {
+        y = start / W_;
+        x = start - y * W_;
+        sy = stride / W_;
+        sx = stride - sy * W_;
     }
-    float f = ((float)pos - c0) / (float)s;
-    f = fminf(fmaxf(f, 0.f), (float)(n - 1));
-    int ia = (int)floorf(f);
-    if (ia > n - 2) ia = n - 2;
-    i0 = ia;
-    t = f - (float)ia;
-}
+    __device__ __forceinline__ void next()
+    {
+        x += sx;
+        y += sy;
+        if (x >= W) {
+            x -= W;
+            ++y;
+        }
+    }
+};
 
 template <typename T>
 __device__ __forceinline__ float ld_px(const unsigned char *img, long long pitch, int x, int y)
@@ -65,25 +69,11 @@ __device__ __forceinline__ float ld_px(const unsigned char *img, long long pitch
     return (float)__ldg(reinterpret_cast<const T *>(img + (long long)y * pitch) + x);
 }
 
-// Bilinear sample of the image at (x + dx, y + dy), clamp-to-edge; x, y integer.
-template <typename T>
-__device__ __forceinline__ float sample_img(const unsigned char *img, long long pitch, int W, int H, int x, int y,
-                                            float dx, float dy)
+template <int PREC>
+__device__ __forceinline__ uint16_t to_h16(float x)
 {
-    // non-finite or absurd displacements are clamped so that the integer
-    // arithmetic below cannot overflow
-    dx = isfinite(dx) ? fminf(fmaxf(dx, -1048576.f), 1048576.f) : 0.f;
-    dy = isfinite(dy) ? fminf(fmaxf(dy, -1048576.f), 1048576.f) : 0.f;
-    const float fx = floorf(dx), fy = floorf(dy);
-    const float tx = dx - fx, ty = dy - fy;
-    const int ix = x + (int)fx, iy = y + (int)fy;
-    const int x0 = min(max(ix, 0), W - 1), x1 = min(max(ix + 1, 0), W - 1);
-    const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
-    const float b00 = ld_px<T>(img, pitch, x0, y0), b10 = ld_px<T>(img, pitch, x1, y0);
-    const float b01 = ld_px<T>(img, pitch, x0, y1), b11 = ld_px<T>(img, pitch, x1, y1);
-    const float top = b00 + tx * (b10 - b00);
-    const float bot = b01 + tx * (b11 - b01);
-    return top + ty * (bot - top);
+    if (PREC == PREC_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
 }
 
 struct TileGeom {
@@ -93,159 +83,183 @@ struct TileGeom {
     int BC, BR, OFFB;
     int hw, vh;
     int nbx, nby, nb;
-    int nodes_w;  // nodes per row in the local node grid
-    int i_lo, j_lo;
 };
 
-// ----------------------------------------------------------- phases 0..2 --
+// Rows of each 16-bit B' copy: the A fragments of an m-tile stack read up to
+// 16 * MT rows below the first row of the last 8-row sub-block.
+__host__ __device__ inline int tc_b_rows(int BR, int ah, int R)
+{
+    const int MT = (8 + 2 * R + 15) / 16;
+    return (BR > ah + 16 * MT ? BR : ah + 16 * MT) + 8;
+}
 
-template <typename T>
-__device__ void load_and_deform(const PassArgs &a, const TileGeom &g, const unsigned char *imgA,
-                                const unsigned char *imgB, bool has_pred, const float *nodes, const int *ti,
-                                const float *tf, float *As, float *Bs, float *red, float &muT_out)
+// ------------------------------------------------------- region loads --
+
+// A region (raw image, or the central-warped frame A'), tile mean mu_T,
+// centred A and B' regions in FP32, and for the tensor-core path their
+// 16-bit copies (B' twice, the second shifted one column left, so that every
+// column pair starts 4-byte aligned).
+template <typename T, int PREC>
+__device__ void load_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs, uint16_t *TA,
+                             uint16_t *TB, float *red)
 {
     const PassPlan &P = a.plan;
     const int tid = threadIdx.x;
     const int R = g.R;
-    // field at a B'-region pixel (logical column bx, row by)
-    auto field = [&](int bx, int by, float &du, float &dv) {
-        if (!has_pred) {
-            du = 0.f;
-            dv = 0.f;
-            return;
-        }
-        const int i0 = ti[bx], j0 = ti[g.BC + by];
-        const float tx = tf[bx], ty = tf[g.BC + by];
-        const int i1 = i0 + (a.nx > 1 ? 1 : 0), j1 = j0 + (a.ny > 1 ? 1 : 0);
-        const float *nu = nodes, *nv = nodes + P.node_cap;
-        const int q = g.nodes_w;
-        float t0 = nu[j0 * q + i0] + tx * (nu[j0 * q + i1] - nu[j0 * q + i0]);
-        float t1 = nu[j1 * q + i0] + tx * (nu[j1 * q + i1] - nu[j1 * q + i0]);
-        du = t0 + ty * (t1 - t0);
-        t0 = nv[j0 * q + i0] + tx * (nv[j0 * q + i1] - nv[j0 * q + i0]);
-        t1 = nv[j1 * q + i0] + tx * (nv[j1 * q + i1] - nv[j1 * q + i0]);
-        dv = t0 + ty * (t1 - t0);
-    };
-    // A region (central mode: A warped by -d/2)
+    const float *adef = (const float *)resolve(a.adef, pair);
+    const float *bdef = (const float *)resolve(a.bdef, pair);
+    const unsigned char *imgA = (const unsigned char *)resolve(a.img_a, pair);
+    const long long dp = a.def_pitch;
+    const int M = a.def_margin;
     float local = 0.f;
-    const int na = g.aw * g.ah;
-    for (int e = tid; e < na; e += blockDim.x) {
-        const int y = e / g.aw, x = e - y * g.aw;
-        float val;
-        if (a.deform == 1 && has_pred) {
-            float du, dv;
-            field(x + R + 1, y + R + 1, du, dv);
-            val = sample_img<T>(imgA, a.pitch, a.W, a.H, g.ax0 + x, g.ay0 + y, -0.5f * du, -0.5f * dv);
-        } else {
-            val = ld_px<T>(imgA, a.pitch, g.ax0 + x, g.ay0 + y);
-        }
-        As[y * P.a_pitch + x] = val;
-        local += val;
+    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next()) {
+        const int x = g.ax0 + it.x, y = g.ay0 + it.y;
+        const float v = adef ? adef[(long long)(y + M) * dp + (x + M)] : ld_px<T>(imgA, a.pitch, x, y);
+        As[it.y * P.a_pitch + it.x] = v;
+        local += v;
     }
-    // tile mean of A: the common offset removed from A and B' (ZNCC is
-    // invariant to it; it keeps the FP32 box sums well conditioned)
     local = warp_sum(local);
     if ((tid & 31) == 0) red[tid >> 5] = local;
     __syncthreads();
     if (tid < 32) {
         float v = tid < (int)(blockDim.x >> 5) ? red[tid] : 0.f;
         v = warp_sum(v);
-        if (tid == 0) red[32] = v / (float)na;
+        if (tid == 0) red[32] = v / (float)(g.aw * g.ah);
     }
     __syncthreads();
     const float muT = red[32];
-    muT_out = muT;
-    for (int e = tid; e < na; e += blockDim.x) {
-        const int y = e / g.aw, x = e - y * g.aw;
-        As[y * P.a_pitch + x] -= muT;
+    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next()) {
+        const float v = As[it.y * P.a_pitch + it.x] - muT;
+        As[it.y * P.a_pitch + it.x] = v;
+        if (PREC != PREC_FP32) TA[it.y * P.tca_pitch + it.x] = to_h16<PREC>(v);
     }
-    const float scale = (a.deform == 1) ? 0.5f : 1.0f;
-    const int nbp = g.BC * g.BR;
-    for (int e = tid; e < nbp; e += blockDim.x) {
-        const int by = e / g.BC, bx = e - by * g.BC;
-        float du, dv;
-        field(bx, by, du, dv);
-        const int x = g.ax0 - (R + 1) + bx, y = g.ay0 - (R + 1) + by;
-        Bs[by * P.b_pitch + g.OFFB + bx] = sample_img<T>(imgB, a.pitch, a.W, a.H, x, y, scale * du, scale * dv) - muT;
+    const int brows = tc_b_rows(g.BR, g.ah, R);
+    uint16_t *TB1 = TB + brows * P.tcb_pitch;
+    const float *src = bdef + (long long)(g.ay0 - (R + 1) + M) * dp + (g.ax0 - (R + 1) + M);
+    for (Walk2D it(tid, blockDim.x, g.BC); it.y < g.BR; it.next()) {
+        const float v = src[(long long)it.y * dp + it.x] - muT;
+        Bs[it.y * P.b_pitch + g.OFFB + it.x] = v;
+        if (PREC != PREC_FP32) {
+            const uint16_t h = to_h16<PREC>(v);
+            TB[it.y * P.tcb_pitch + g.OFFB + it.x] = h;
+            if (g.OFFB + it.x >= 1) TB1[it.y * P.tcb_pitch + g.OFFB + it.x - 1] = h;
+        }
+    }
+    if (PREC != PREC_FP32) {
+        // zero the part of the copies that fragments may touch outside the region
+        const int c_lo = g.OFFB + g.BC - 1, c_n = 9;
+        for (Walk2D it(tid, blockDim.x, c_n); it.y < g.BR; it.next()) {
+            if (it.x > 0) TB[it.y * P.tcb_pitch + c_lo + it.x] = 0;
+            TB1[it.y * P.tcb_pitch + c_lo + it.x] = 0;
+        }
+        for (Walk2D it(tid, blockDim.x, P.tcb_pitch); it.y < brows - g.BR; it.next()) {
+            TB[(g.BR + it.y) * P.tcb_pitch + it.x] = 0;
+            TB1[(g.BR + it.y) * P.tcb_pitch + it.x] = 0;
+        }
     }
 }
 
-// ------------------------------------------------------ box sums (H, V) --
+// ------------------------------------------------------ box sums (C, V) --
 
-static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Hs, float *Vs)
+// Window box sums of B' and B'^2 at every shift, in two sliding passes:
+//   C[r][x] = sum_{y=r}^{r+w-1} B'[y][x]        (threads along x: conflict free)
+//   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]         (threads along r, odd pitch)
+// so V[r][c] is the sum over the w x w box whose top-left logical B' pixel
+// is (r, c).  Each thread restarts its running sum every 8 outputs.
+static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
 {
     const PassPlan &P = a.plan;
     const int w = a.w, tid = threadIdx.x;
-    // H[r][c] = sum_{x=c}^{c+w-1} B'[r][x] (logical columns), segments of 8
-    const int nseg = (g.hw + 7) / 8;
-    for (int it = tid; it < g.BR * nseg; it += blockDim.x) {
-        const int by = it / nseg, seg = it - by * nseg;
-        const int c_lo = seg * 8, c_hi = min(g.hw, c_lo + 8);
-        const float *row = Bs + by * P.b_pitch + g.OFFB;
+    const int cp = P.h_pitch;  // pitch of C and V (odd)
+    float *C1 = Cs, *C2 = Cs + g.vh * cp;
+    const int nsegv = (g.vh + 7) / 8;
+    for (int it = tid; it < g.BC * nsegv; it += blockDim.x) {
+        const int seg = it / g.BC, x = it - seg * g.BC;
+        const int r_lo = seg * 8, r_hi = min(g.vh, r_lo + 8);
+        const float *col = Bs + g.OFFB + x;
         float s1 = 0.f, s2 = 0.f;
-        for (int x = c_lo; x < c_lo + w; ++x) {
-            const float b = row[x];
+        for (int y = r_lo; y < r_lo + w; ++y) {
+            const float b = col[y * P.b_pitch];
             s1 += b;
             s2 = fmaf(b, b, s2);
         }
-        float *h1 = Hs + by * P.h_pitch;
-        float *h2 = Hs + (g.BR + by) * P.h_pitch;
-        h1[c_lo] = s1;
-        h2[c_lo] = s2;
-        for (int c = c_lo + 1; c < c_hi; ++c) {
-            const float bo = row[c - 1], bi = row[c + w - 1];
+        C1[r_lo * cp + x] = s1;
+        C2[r_lo * cp + x] = s2;
+        for (int r = r_lo + 1; r < r_hi; ++r) {
+            const float bo = col[(r - 1) * P.b_pitch], bi = col[(r + w - 1) * P.b_pitch];
             s1 += bi - bo;
             s2 += bi * bi - bo * bo;
-            h1[c] = s1;
-            h2[c] = s2;
+            C1[r * cp + x] = s1;
+            C2[r * cp + x] = s2;
         }
     }
     __syncthreads();
-    // V[r][c] = sum_{y=r}^{r+w-1} H[y][c], segments of 8 rows
-    const int nsegv = (g.vh + 7) / 8;
-    for (int it = tid; it < g.hw * nsegv; it += blockDim.x) {
-        const int c = it / nsegv, seg = it - c * nsegv;
-        const int r_lo = seg * 8, r_hi = min(g.vh, r_lo + 8);
-        const float *h1 = Hs + c, *h2 = Hs + g.BR * P.h_pitch + c;
+    float *V1 = Vs, *V2 = Vs + g.vh * cp;
+    const int nsegh = (g.hw + 7) / 8;
+    for (int it = tid; it < g.vh * nsegh; it += blockDim.x) {
+        const int seg = it / g.vh, r = it - seg * g.vh;
+        const int c_lo = seg * 8, c_hi = min(g.hw, c_lo + 8);
+        const float *c1 = C1 + r * cp, *c2 = C2 + r * cp;
         float s1 = 0.f, s2 = 0.f;
-        for (int y = r_lo; y < r_lo + w; ++y) {
-            s1 += h1[y * P.h_pitch];
-            s2 += h2[y * P.h_pitch];
+        for (int x = c_lo; x < c_lo + w; ++x) {
+            s1 += c1[x];
+            s2 += c2[x];
         }
-        float *v1 = Vs + c, *v2 = Vs + g.vh * P.h_pitch + c;
-        v1[r_lo * P.h_pitch] = s1;
-        v2[r_lo * P.h_pitch] = s2;
-        for (int r = r_lo + 1; r < r_hi; ++r) {
-            s1 += h1[(r + w - 1) * P.h_pitch] - h1[(r - 1) * P.h_pitch];
-            s2 += h2[(r + w - 1) * P.h_pitch] - h2[(r - 1) * P.h_pitch];
-            v1[r * P.h_pitch] = s1;
-            v2[r * P.h_pitch] = s2;
+        V1[r * cp + c_lo] = s1;
+        V2[r * cp + c_lo] = s2;
+        for (int c = c_lo + 1; c < c_hi; ++c) {
+            s1 += c1[c + w - 1] - c1[c - 1];
+            s2 += c2[c + w - 1] - c2[c - 1];
+            V1[r * cp + c] = s1;
+            V2[r * cp + c] = s2;
         }
     }
 }
 
-// Per-window mean and energy of A_c (two-pass, one warp per window).
-static __device__ void window_stats(const PassArgs &a, const TileGeom &g, const float *As, float *stats)
+// Sum and centred sum of squares of every 8-row group of every A window; one
+// warp per (window, group), lanes along the columns, two passes.
+static __device__ void window_group_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *gst)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int w = a.w, n = w * w;
-    for (int wi = warp; wi < g.nwin; wi += nwarps) {
+    const int w = a.w, ngr = (w + 7) / 8;
+    for (int it = warp; it < g.nwin * ngr; it += nwarps) {
+        const int wi = it / ngr, gr = it - wi * ngr;
         const int wxi = wi % g.nwx, wyi = wi / g.nwx;
-        const float *base = As + (wyi * a.s) * P.a_pitch + wxi * a.s;
+        const int rows = min(8, w - 8 * gr);
+        const float *base = As + (wyi * a.s + 8 * gr) * P.a_pitch + wxi * a.s;
         float s = 0.f;
-        for (int e = lane; e < n; e += 32) s += base[(e / w) * P.a_pitch + (e % w)];
-        const float mean = warp_sum(s) / (float)n;
+        for (Walk2D e(lane, 32, w); e.y < rows; e.next()) s += base[e.y * P.a_pitch + e.x];
+        s = warp_sum(s);
+        const float m = s / (float)(rows * w);
         float q = 0.f;
-        for (int e = lane; e < n; e += 32) {
-            const float d = base[(e / w) * P.a_pitch + (e % w)] - mean;
+        for (Walk2D e(lane, 32, w); e.y < rows; e.next()) {
+            const float d = base[e.y * P.a_pitch + e.x] - m;
             q = fmaf(d, d, q);
         }
         q = warp_sum(q);
-        if (lane == 0) {
-            stats[2 * wi] = mean;
-            stats[2 * wi + 1] = q;
+        if (lane == 0) gst[it] = make_float2(s, q);
+    }
+}
+
+// Window mean and energy from its groups: E = sum M2_g + sum n_g (mean_g - mean)^2.
+static __device__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *gst, float *stats)
+{
+    const int w = a.w, ngr = (w + 7) / 8;
+    const float n = (float)(w * w);
+    for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
+        float s = 0.f;
+        for (int gr = 0; gr < ngr; ++gr) s += gst[wi * ngr + gr].x;
+        const float mean = s / n;
+        float e = 0.f;
+        for (int gr = 0; gr < ngr; ++gr) {
+            const float ng = (float)(min(8, w - 8 * gr) * w);
+            const float2 p = gst[wi * ngr + gr];
+            const float d = p.x / ng - mean;
+            e += p.y + ng * d * d;
         }
+        stats[2 * wi] = mean;
+        stats[2 * wi + 1] = e;
     }
 }
 
@@ -342,12 +356,6 @@ static __device__ void block_planes_fp32_generic(const PassArgs &a, const TileGe
 
 // ------------------------------------------- tensor-core block planes --
 
-template <int PREC>
-__device__ __forceinline__ uint16_t to_h16(float x)
-{
-    if (PREC == PREC_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-    return __half_as_ushort(__float2half_rn(x));
-}
 
 template <int PREC>
 __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0)
@@ -365,32 +373,6 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
     }
 }
 
-// 16-bit copies for the tensor-core path: A_c, and B'_c twice (the second
-// shifted by one column so that every pair of columns starts 4-byte aligned).
-template <int PREC>
-__device__ void tc_convert(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, uint16_t *TA,
-                           uint16_t *TB)
-{
-    const PassPlan &P = a.plan;
-    const int tid = threadIdx.x;
-    const int arows = ((g.ah + 7) / 8) * 8 + 8;
-    for (int e = tid; e < arows * P.tca_pitch; e += blockDim.x) {
-        const int y = e / P.tca_pitch, x = e - y * P.tca_pitch;
-        const float v = (y < g.ah && x < g.aw) ? As[y * P.a_pitch + x] : 0.f;
-        TA[e] = to_h16<PREC>(v);
-    }
-    const int brows = g.BR + 32;
-    const int lo = g.OFFB, hi = g.OFFB + g.BC;
-    uint16_t *TB1 = TB + brows * P.tcb_pitch;
-    for (int e = tid; e < brows * P.tcb_pitch; e += blockDim.x) {
-        const int y = e / P.tcb_pitch, x = e - y * P.tcb_pitch;
-        const float v0 = (y < g.BR && x >= lo && x < hi) ? Bs[y * P.b_pitch + x] : 0.f;
-        const float v1 = (y < g.BR && x + 1 >= lo && x + 1 < hi) ? Bs[y * P.b_pitch + x + 1] : 0.f;
-        TB[e] = to_h16<PREC>(v0);
-        TB1[e] = to_h16<PREC>(v1);
-    }
-}
-
 // One warp per (block, 8-row sub-block).  For each chunk of at most 9 shifts
 // sx the accumulators D[i][j] (i: B' row offset, j: A row offset) are summed
 // over the sub-block's 8-column chunks; shift sy = i - j - R is recovered from
@@ -402,15 +384,15 @@ __device__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint
     constexpr int ND = 2 * R + 1;
     constexpr int NP = ND * ND;
     constexpr int MT = (8 + 2 * R + 15) / 16;
-    constexpr int SXC = ND < 9 ? ND : 9;
+    constexpr int SXC = ND < 3 ? ND : 3;
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
     const int G = P.G;
     const int nsb = (G + 7) / 8, nkc = (G + 7) / 8;
-    const int brows = g.BR + 32;
+    const int brows = tc_b_rows(g.BR, g.ah, R);
     const uint16_t *TB1 = TB + brows * P.tcb_pitch;
-    float *scr = scratch + warp * (SXC * ND * 8);
+    float *scr = scratch + warp * (SXC * 16 * MT * 9);
     const int items = g.nb * nsb;
     for (int it = warp; it < items; it += nwarps) {
         const int b = it / nsb, sb = it - b * nsb;
@@ -451,34 +433,35 @@ __device__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint
                     }
                 }
             }
-            // scatter the diagonals d = i - j in [0, 2R] to scr[q][d][j]
+            // store the accumulator tiles (row pitch 9: conflict-free diagonal reads)
 #pragma unroll
             for (int q = 0; q < SXC; ++q) {
 #pragma unroll
                 for (int m = 0; m < MT; ++m) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int i = 16 * m + gq + ((e & 2) ? 8 : 0);
-                        const int j = 2 * tq + (e & 1);
-                        const int d = i - j;
-                        if (d >= 0 && d < ND) scr[(q * ND + d) * 8 + j] = acc[q][m][e];
-                    }
+                    float *t = scr + (q * 16 * MT + 16 * m) * 9;
+                    t[gq * 9 + 2 * tq] = acc[q][m][0];
+                    t[gq * 9 + 2 * tq + 1] = acc[q][m][1];
+                    t[(gq + 8) * 9 + 2 * tq] = acc[q][m][2];
+                    t[(gq + 8) * 9 + 2 * tq + 1] = acc[q][m][3];
                 }
             }
             __syncwarp();
+            // shift sy = d - R is the diagonal i - j = d of the tile
             const int nq = min(SXC, R - sx0 + 1);
             for (int o = lane; o < nq * ND; o += 32) {
                 const int q = o / ND, d = o - q * ND;
-                const float4 lo4 = *reinterpret_cast<const float4 *>(scr + (q * ND + d) * 8);
-                const float4 hi4 = *reinterpret_cast<const float4 *>(scr + (q * ND + d) * 8 + 4);
-                const float sum = ((lo4.x + lo4.y) + (lo4.z + lo4.w)) + ((hi4.x + hi4.y) + (hi4.z + hi4.w));
-                // plane index: sy = d - R -> row d; sx = sx0 + q -> column sx0 + q + R
+                const float *t = scr + q * 16 * MT * 9 + d * 9;
+                float sum = 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) sum += t[j * 10];
                 Ps[(size_t)(b * nsb + sb) * NP + d * ND + (sx0 + q + R)] = sum;
             }
             __syncwarp();
         }
     }
 }
+
+
 
 // ----------------------------------------------- assembly and sub-pixel --
 
@@ -505,92 +488,73 @@ __device__ __forceinline__ float gauss3f(float cm, float c0, float cp)
     return fminf(fmaxf(d, -1.f), 1.f);
 }
 
-struct WinRef {
-    int wxi, wyi;       // tile-local window index
-    float muA, EA;
-    float inv_n, tau;
+// ZNCC from the numerator sum A_c B'_c, the window's mean/energy of A_c and
+// the box sums of B'_c at this shift; degenerate windows give 0.
+__device__ __forceinline__ float zncc_from(float num, float muA, float EA, float S1, float S2, float inv_n, float tau)
+{
+    const float Nc = num - muA * S1;
+    const float EB = S2 - S1 * S1 * inv_n;
+    if (!(EA > tau) || !(EB > tau)) return 0.f;
+    return Nc * rsqrtf(EA * EB);
+}
+
+__device__ __forceinline__ void stencil_shift(int p, int ky, int kx, int &sy, int &sx)
+{
+    // 0 centre, 1 -x, 2 +x, 3 -y, 4 +y
+    sy = ky + (p == 3 ? -1 : (p == 4 ? 1 : 0));
+    sx = kx + (p == 1 ? -1 : (p == 2 ? 1 : 0));
+}
+
+struct WinShared {
+    float *c5;    // [nwin][5] stencil values (plane-supplied ones)
+    int *peaks;   // [nwin] plane index of the argmax
+    int *need;    // [nwin] bit p set: stencil point p needs a direct FP32 sum
+    float *dpart; // [nwin][ngr][5] direct numerators per 8-row group
 };
 
-__device__ __forceinline__ float zncc_from(float num, const WinRef &wr, float S1, float S2)
-{
-    const float Nc = num - wr.muA * S1;
-    const float EB = S2 - S1 * S1 * wr.inv_n;
-    if (!(wr.EA > wr.tau) || !(EB > wr.tau)) return 0.f;
-    return Nc / sqrtf(wr.EA * EB);
-}
-
-// numerator of one window at shift (sy, sx) by direct FP32 summation (warp-wide)
-static __device__ float direct_num(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, const WinRef &wr,
-                            int sy, int sx)
-{
-    const PassPlan &P = a.plan;
-    const int lane = threadIdx.x & 31, w = a.w, n = w * w;
-    const float *abase = As + (wr.wyi * a.s) * P.a_pitch + wr.wxi * a.s;
-    const float *bbase = Bs + (wr.wyi * a.s + sy + g.R + 1) * P.b_pitch + P.padl + wr.wxi * a.s + sx;
-    float acc = 0.f;
-    for (int e = lane; e < n; e += 32) {
-        const int y = e / w, x = e - y * w;
-        acc = fmaf(abase[y * P.a_pitch + x], bbase[y * P.b_pitch + x], acc);
-    }
-    return warp_sum(acc);
-}
-
-__device__ __forceinline__ float plane_num(const PassArgs &a, const TileGeom &g, const float *Ps, const WinRef &wr,
-                                           int q)
-{
-    const PassPlan &P = a.plan;
-    const int G = P.G, kb = a.w / G, RG = P.RGx;
-    const int bx0 = (wr.wxi * a.s) / G, by0 = (wr.wyi * a.s) / G;
-    float sum = 0.f;
-    for (int yy = 0; yy < kb; ++yy)
-        for (int xx = 0; xx < kb; ++xx) {
-            const float *pb = Ps + (size_t)((by0 + yy) * g.nbx + bx0 + xx) * RG * g.NP + q;
-            for (int gi = 0; gi < RG; ++gi) sum += pb[(size_t)gi * g.NP];
-        }
-    return sum;
-}
-
-// Window assembly, argmax, 5-point FP32 stencil, Gaussian fit; one warp per window.
-static __device__ void assemble(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, const float *Vs,
-                         const float *Ps, const float *stats, bool tc, int pair)
+// One warp per window: plane from the block planes and box sums, argmax
+// (ties keep the smallest row-major index), plane values of the stencil.
+// RC >= 0: compile-time radius (shift decoding without integer division).
+template <int RC>
+static __device__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
+                                      const float *stats, bool tc, const WinShared &ws)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int R = g.R, ND = g.ND, NP = g.NP;
-    const float n = (float)(a.w * a.w);
-    const float *pu = (const float *)resolve(a.pred_u, pair);
-    const float *pv = (const float *)resolve(a.pred_v, pair);
-    float *ou = (float *)resolve(a.out_u, pair);
-    float *ov = (float *)resolve(a.out_v, pair);
-    int32_t *oi = (int32_t *)resolve(a.out_info, pair);
-    const float *V1 = Vs, *V2 = Vs + g.vh * P.h_pitch;
+    const int R = RC >= 0 ? RC : g.R;
+    const int ND = 2 * R + 1, NP = ND * ND;
+    const int G = P.G, kb = a.w / G, RG = P.RGx;
+    const float inv_n = 1.f / (float)(a.w * a.w), tau = TAU_PER_PIXEL * (float)(a.w * a.w);
+    const int cp = P.h_pitch;
+    const float *V1 = Vs, *V2 = Vs + g.vh * cp;
     for (int wi = warp; wi < g.nwin; wi += nwarps) {
-        WinRef wr;
-        wr.wxi = wi % g.nwx;
-        wr.wyi = wi / g.nwx;
-        wr.muA = stats[2 * wi];
-        wr.EA = stats[2 * wi + 1];
-        wr.inv_n = 1.f / n;
-        wr.tau = TAU_PER_PIXEL * n;
-        const int gi = (g.wy0 + wr.wyi), gj = (g.wx0 + wr.wxi);
-        const int k = gi * a.nx + gj;
-        const float pu0 = pu ? pu[k] : 0.f, pv0 = pv ? pv[k] : 0.f;
-        const int vr0 = wr.wyi * a.s + R + 1, vc0 = wr.wxi * a.s + R + 1;
-        auto S1at = [&](int sy, int sx) { return V1[(vr0 + sy) * P.h_pitch + vc0 + sx]; };
-        auto S2at = [&](int sy, int sx) { return V2[(vr0 + sy) * P.h_pitch + vc0 + sx]; };
-        if (!(wr.EA > wr.tau)) {
-            if (lane == 0) {
-                ou[k] = pu0;
-                ov[k] = pv0;
-                oi[k] = 0;
+        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
+        const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
+        const int bx0 = (wxi * a.s) / G, by0 = (wyi * a.s) / G;
+        const float *v1 = V1 + (wyi * a.s + R + 1) * cp + wxi * a.s + R + 1;
+        const float *v2 = V2 + (wyi * a.s + R + 1) * cp + wxi * a.s + R + 1;
+        // the window's partial planes: for each of its kb block rows, kb * RG
+        // consecutive planes of NP floats
+        const float *prow = Ps + (size_t)(by0 * g.nbx + bx0) * RG * NP;
+        const int run = kb * RG, row_stride = g.nbx * RG * NP;
+        auto cval = [&](int q) {
+            const int qy = q / ND;
+            const int sy = qy - R, sx = q - qy * ND - R;
+            float num = 0.f;
+            for (int yy = 0; yy < kb; ++yy) {
+                const float *pr = prow + (size_t)yy * row_stride + q;
+                for (int t = 0; t < run; ++t) num += pr[t * NP];
             }
-            continue;
-        }
+            const float S1 = v1[sy * cp + sx], S2 = v2[sy * cp + sx];
+            const float Nc = num - muA * S1;
+            const float EB = S2 - S1 * S1 * inv_n;
+            if (!(EA > tau) || !(EB > tau)) return 0.f;
+            return Nc * rsqrtf(EA * EB);
+        };
         float best = -INFINITY;
         int bidx = 0x7fffffff;
         for (int q = lane; q < NP; q += 32) {
-            const int sy = q / ND - R, sx = q % ND - R;
-            const float c = zncc_from(plane_num(a, g, Ps, wr, q), wr, S1at(sy, sx), S2at(sy, sx));
+            const float c = cval(q);
             if (c > best || (c == best && q < bidx)) {
                 best = c;
                 bidx = q;
@@ -605,27 +569,110 @@ static __device__ void assemble(const PassArgs &a, const TileGeom &g, const floa
                 bidx = oq;
             }
         }
+        if (bidx < 0 || bidx >= NP) bidx = NP / 2;  // non-finite plane: zero shift
         const int ky = bidx / ND - R, kx = bidx % ND - R;
-        // 5-point stencil in FP32: centre, -x, +x, -y, +y
+        if (lane < 5) {
+            int sy, sx;
+            stencil_shift(lane, ky, kx, sy, sx);
+            const bool inside = sy >= -R && sy <= R && sx >= -R && sx <= R;
+            const bool direct = tc || !inside;
+            ws.c5[wi * 5 + lane] = direct ? 0.f : cval((sy + R) * ND + (sx + R));
+            const unsigned bits = __ballot_sync(0x1fu, direct);
+            if (lane == 0) {
+                ws.peaks[wi] = bidx;
+                ws.need[wi] = (int)bits;
+            }
+        }
+    }
+}
+
+// Direct FP32 numerators of the stencil points the plane cannot supply: one
+// warp per (window, 8-row group), lanes along the columns, five accumulators.
+static __device__ void stencil_direct(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs,
+                                      const WinShared &ws)
+{
+    const PassPlan &P = a.plan;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int w = a.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
+    for (int it = warp; it < g.nwin * ngr; it += nwarps) {
+        const int wi = it / ngr, gr = it - wi * ngr;
+        const int need = ws.need[wi];
+        if (!need) continue;
+        const int q = ws.peaks[wi];
+        const int ky = q / ND - R, kx = q % ND - R;
+        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
+        const int rows = min(8, w - 8 * gr);
+        const float *abase = As + (wyi * a.s + 8 * gr) * P.a_pitch + wxi * a.s;
+        // B' at A pixel (r, x) and shift (sy, sx): row r + sy + R + 1, column x + sx + padl
+        const float *bbase = Bs + (wyi * a.s + 8 * gr + ky + R + 1) * P.b_pitch + P.padl + wxi * a.s + kx;
+        float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (Walk2D e(lane, 32, w); e.y < rows; e.next()) {
+            const float av = abase[e.y * P.a_pitch + e.x];
+            const float *bb = bbase + e.y * P.b_pitch + e.x;
+            if (need & 1) acc[0] = fmaf(av, bb[0], acc[0]);
+            if (need & 2) acc[1] = fmaf(av, bb[-1], acc[1]);
+            if (need & 4) acc[2] = fmaf(av, bb[1], acc[2]);
+            if (need & 8) acc[3] = fmaf(av, bb[-P.b_pitch], acc[3]);
+            if (need & 16) acc[4] = fmaf(av, bb[P.b_pitch], acc[4]);
+        }
+#pragma unroll
+        for (int p = 0; p < 5; ++p) acc[p] = warp_sum(acc[p]);
+        if (lane < 5) {
+            float v = acc[0];
+#pragma unroll
+            for (int p = 1; p < 5; ++p)
+                if (lane == p) v = acc[p];
+            ws.dpart[(wi * ngr + gr) * 5 + lane] = v;
+        }
+    }
+}
+
+// Stencil values, Gaussian fit and outputs (one thread per window).
+static __device__ void finalize(const PassArgs &a, const TileGeom &g, const float *Vs, const float *stats,
+                                const WinShared &ws, int pair)
+{
+    const PassPlan &P = a.plan;
+    const int w = a.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
+    const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
+    const int cp = P.h_pitch;
+    const float *V1 = Vs, *V2 = Vs + g.vh * cp;
+    const float *pu = (const float *)resolve(a.pred_u, pair);
+    const float *pv = (const float *)resolve(a.pred_v, pair);
+    float *ou = (float *)resolve(a.out_u, pair);
+    float *ov = (float *)resolve(a.out_v, pair);
+    int32_t *oi = (int32_t *)resolve(a.out_info, pair);
+    for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
+        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
+        const int k = (g.wy0 + wyi) * a.nx + (g.wx0 + wxi);
+        const float pu0 = pu ? pu[k] : 0.f, pv0 = pv ? pv[k] : 0.f;
+        const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
+        if (!(EA > tau)) {
+            ou[k] = pu0;
+            ov[k] = pv0;
+            oi[k] = 0;
+            continue;
+        }
+        const int q = ws.peaks[wi], need = ws.need[wi];
+        const int ky = q / ND - R, kx = q % ND - R;
         float c5[5];
-        const int dys[5] = {0, 0, 0, -1, 1}, dxs[5] = {0, -1, 1, 0, 0};
 #pragma unroll
         for (int p = 0; p < 5; ++p) {
-            const int sy = ky + dys[p], sx = kx + dxs[p];
-            float num;
-            if (!tc && sy >= -R && sy <= R && sx >= -R && sx <= R)
-                num = plane_num(a, g, Ps, wr, (sy + R) * ND + (sx + R));
-            else
-                num = direct_num(a, g, As, Bs, wr, sy, sx);
-            c5[p] = zncc_from(num, wr, S1at(sy, sx), S2at(sy, sx));
+            if (need & (1 << p)) {
+                int sy, sx;
+                stencil_shift(p, ky, kx, sy, sx);
+                float num = 0.f;
+                for (int gr = 0; gr < ngr; ++gr) num += ws.dpart[(wi * ngr + gr) * 5 + p];
+                const int vo = (wyi * a.s + R + 1 + sy) * cp + wxi * a.s + R + 1 + sx;
+                c5[p] = zncc_from(num, muA, EA, V1[vo], V2[vo], inv_n, tau);
+            } else {
+                c5[p] = ws.c5[wi * 5 + p];
+            }
         }
-        if (lane == 0) {
-            const float dx = gauss3f(c5[1], c5[0], c5[2]);
-            const float dy = gauss3f(c5[3], c5[0], c5[4]);
-            ou[k] = pu0 + (float)kx + dx;
-            ov[k] = pv0 + (float)ky + dy;
-            oi[k] = 1 | ((int)(uint8_t)(int8_t)ky << 8) | ((int)(uint8_t)(int8_t)kx << 16);
-        }
+        const float dx = gauss3f(c5[1], c5[0], c5[2]);
+        const float dy = gauss3f(c5[3], c5[0], c5[4]);
+        ou[k] = pu0 + (float)kx + dx;
+        ov[k] = pv0 + (float)ky + dy;
+        oi[k] = 1 | ((int)(uint8_t)(int8_t)ky << 8) | ((int)(uint8_t)(int8_t)kx << 16);
     }
 }
 
@@ -660,97 +707,56 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
     g.nby = g.ah / P.G;
     g.nb = g.nbx * g.nby;
 
-    float *nodes = reinterpret_cast<float *>(smem + P.off_nodes);
-    int *ti = reinterpret_cast<int *>(smem + P.off_tabs);
-    float *tf = reinterpret_cast<float *>(ti + g.BC + g.BR);
     float *As = reinterpret_cast<float *>(smem + P.off_a);
     float *Bs = reinterpret_cast<float *>(smem + P.off_b);
-    float *Hs = reinterpret_cast<float *>(smem + P.off_h);
+    float *Cs = reinterpret_cast<float *>(smem + P.off_h);
     float *Vs = reinterpret_cast<float *>(smem + P.off_v);
     float *Ps = reinterpret_cast<float *>(smem + P.off_p);
     float *stats = reinterpret_cast<float *>(smem + P.off_stats);
     float *red = reinterpret_cast<float *>(smem + P.off_red);
+    float2 *gst = reinterpret_cast<float2 *>(smem + P.off_gst);
+    uint16_t *TA = reinterpret_cast<uint16_t *>(smem + P.off_tca);
+    uint16_t *TB = reinterpret_cast<uint16_t *>(smem + P.off_tcb);
+    WinShared ws;
+    ws.c5 = reinterpret_cast<float *>(smem + P.off_c5);
+    ws.peaks = reinterpret_cast<int *>(smem + P.off_peaks);
+    ws.need = reinterpret_cast<int *>(smem + P.off_need);
+    ws.dpart = reinterpret_cast<float *>(smem + P.off_dpart);
 
-    const unsigned char *imgA = (const unsigned char *)resolve(a.img_a, pair);
-    const unsigned char *imgB = (const unsigned char *)resolve(a.img_b, pair);
-    const float *pu = (const float *)resolve(a.pred_u, pair);
-    const float *pv = (const float *)resolve(a.pred_v, pair);
-    const bool has_pred = (pu != nullptr) && (pv != nullptr);
-    const int tid = threadIdx.x;
-    const float c0 = 0.5f * (float)(w - 1);
-
-    // phase 0: grid weights of every region column/row and the predictor nodes
-    {
-        int ilo, ihi, jlo, jhi;
-        float t;
-        axis_w(g.ax0 - (g.R + 1), a.nx, c0, s, ilo, t);
-        axis_w(g.ax0 - (g.R + 1) + g.BC - 1, a.nx, c0, s, ihi, t);
-        axis_w(g.ay0 - (g.R + 1), a.ny, c0, s, jlo, t);
-        axis_w(g.ay0 - (g.R + 1) + g.BR - 1, a.ny, c0, s, jhi, t);
-        ihi = min(ihi + 1, a.nx - 1);
-        jhi = min(jhi + 1, a.ny - 1);
-        g.i_lo = ilo;
-        g.j_lo = jlo;
-        g.nodes_w = ihi - ilo + 1;
-        const int nh = jhi - jlo + 1;
-        for (int bx = tid; bx < g.BC; bx += blockDim.x) {
-            int i0;
-            float tt;
-            axis_w(g.ax0 - (g.R + 1) + bx, a.nx, c0, s, i0, tt);
-            ti[bx] = i0 - ilo;
-            tf[bx] = tt;
-        }
-        for (int by = tid; by < g.BR; by += blockDim.x) {
-            int j0;
-            float tt;
-            axis_w(g.ay0 - (g.R + 1) + by, a.ny, c0, s, j0, tt);
-            ti[g.BC + by] = j0 - jlo;
-            tf[g.BC + by] = tt;
-        }
-        if (has_pred) {
-            for (int e = tid; e < g.nodes_w * nh; e += blockDim.x) {
-                const int jj = e / g.nodes_w, ii = e - jj * g.nodes_w;
-                const int gk = (jlo + jj) * a.nx + ilo + ii;
-                nodes[e] = pu[gk];
-                nodes[P.node_cap + e] = pv[gk];
-            }
-        }
-    }
-    __syncthreads();
-
-    // phases 1-2: A region, tile mean, deformed B' region
-    float muT;
+    // 1: A and B' regions (and their 16-bit copies on the tensor-core path)
     if (a.fmt == PIX_U8)
-        load_and_deform<uint8_t>(a, g, imgA, imgB, has_pred, nodes, ti, tf, As, Bs, red, muT);
+        load_regions<uint8_t, PREC>(a, g, pair, As, Bs, TA, TB, red);
     else if (a.fmt == PIX_U16)
-        load_and_deform<uint16_t>(a, g, imgA, imgB, has_pred, nodes, ti, tf, As, Bs, red, muT);
+        load_regions<uint16_t, PREC>(a, g, pair, As, Bs, TA, TB, red);
     else
-        load_and_deform<float>(a, g, imgA, imgB, has_pred, nodes, ti, tf, As, Bs, red, muT);
+        load_regions<float, PREC>(a, g, pair, As, Bs, TA, TB, red);
     __syncthreads();
 
-    // phase 3-4: box sums of B' for every window and shift; A window statistics
-    window_stats(a, g, As, stats);
-    box_sums(a, g, Bs, Hs, Vs);
+    // 2: A window statistics, box sums of B' for every window and shift
+    window_group_stats(a, g, As, gst);
+    box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
     __syncthreads();
+    window_stats(a, g, gst, stats);
 
-    // phase 5: block partial planes (aliases the dead H region)
+    // 3: block partial planes (alias the dead C region)
     if (PREC == PREC_FP32) {
         if (RC >= 0)
             block_planes_fp32<(RC >= 0 ? RC : 0)>(a, g, As, Bs, Ps);
         else
             block_planes_fp32_generic(a, g, As, Bs, Ps);
     } else {
-        uint16_t *TA = reinterpret_cast<uint16_t *>(smem + P.off_tca);
-        uint16_t *TB = reinterpret_cast<uint16_t *>(smem + P.off_tcb);
         float *scr = reinterpret_cast<float *>(smem + P.off_scr);
-        tc_convert<PREC>(a, g, As, Bs, TA, TB);
-        __syncthreads();
         block_planes_tc<(RC >= 0 ? RC : 0), PREC>(a, g, TA, TB, scr, Ps);
     }
     __syncthreads();
 
-    // phase 6: per-window plane, argmax, refit, Gaussian fit, outputs
-    assemble(a, g, As, Bs, Vs, Ps, stats, PREC != PREC_FP32, pair);
+    // 4: plane, argmax, FP32 stencil, Gaussian fit, outputs
+    constexpr bool tc = PREC != PREC_FP32;
+    plane_and_peak<RC>(a, g, Ps, Vs, stats, tc, ws);
+    __syncthreads();
+    stencil_direct(a, g, As, Bs, ws);
+    __syncthreads();
+    finalize(a, g, Vs, stats, ws, pair);
 }
 
 }  // namespace rpiv

@@ -1,6 +1,7 @@
 // Host-side tiling and shared-memory layout of the fused correlation pass,
 // and dispatch to the per-precision kernel instantiations.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "rpiv_internal.h"
@@ -31,7 +32,17 @@ void prepare_pass_kernels()
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSmemBudget = 110 * 1024;  // two CTAs per SM
+// Shared memory a tile may use: 112 KB keeps two CTAs per SM (228 KB per SM,
+// 1 KB reserved per CTA).  RPIV_TILE_SMEM_KB overrides it (tuning).
+int smem_budget()
+{
+    static int kb = [] {
+        const char *e = std::getenv("RPIV_TILE_SMEM_KB");
+        const int v = e ? std::atoi(e) : 0;
+        return (v >= 16 && v <= 227) ? v : 112;
+    }();
+    return kb * 1024;
+}
 constexpr int kSmemMax = 227 * 1024;
 
 int gcd(int a, int b)
@@ -58,17 +69,23 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     const int ND = 2 * R + 1, NP = ND * ND;
     const int aw = (TX - 1) * s + w, ah = (TY - 1) * s + w;
     const int BC = aw + 2 * (R + 1), BR = ah + 2 * (R + 1);
-    const int hw = BC - w + 1, vh = BR - w + 1;
+    const int vh = BR - w + 1;
     const int nb = (aw / G) * (ah / G);
+    const int nwin = TX * TY, ngr = (w + 7) / 8;
     p.TX = TX;
     p.TY = TY;
     p.G = G;
     p.threads = kThreads;
     p.padl = up(R + 1, 4);
-    p.a_pitch = up(aw, 4);
-    p.b_pitch = up(p.padl + aw + R + 1 + 8, 4);
-    p.h_pitch = up(hw, 4);
-    if (p.h_pitch % 32 == 0) p.h_pitch += 4;
+    // pitches chosen so the dominant access patterns are bank-conflict free:
+    // 128-bit loads down consecutive rows need pitch/4 odd; the scalar sliding
+    // sums along rows need an odd pitch; paired 16-bit loads of 8 rows x 4
+    // words need pitch/2 = 4 (mod 8)
+    auto odd4 = [](int x) { x = up(x, 4); return ((x / 4) % 2) ? x : x + 4; };
+    auto odd8 = [](int x) { x = up(x, 8); return ((x / 8) % 2) ? x : x + 8; };
+    p.a_pitch = odd4(aw);
+    p.b_pitch = odd4(p.padl + aw + R + 4);
+    p.h_pitch = BC | 1;
     if (prec == PREC_FP32) {
         // partial planes per block: enough (block, sy, row-group) items to fill the CTA
         int RG = 1;
@@ -87,39 +104,40 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
         off = up(off + bytes, 16);
         return o;
     };
-    p.node_cap = ((BC + s - 1) / s + 3) * ((BR + s - 1) / s + 3);
-    p.off_nodes = take(2 * p.node_cap * 4);
-    p.off_tabs = take(2 * (BC + BR) * 4);
     p.off_a = take(ah * p.a_pitch * 4);
     p.off_b = take(BR * p.b_pitch * 4);
     p.off_v = take(2 * vh * p.h_pitch * 4);
-    p.off_stats = take(2 * TX * TY * 4);
+    p.off_stats = take(2 * nwin * 4);
     p.off_red = take(40 * 4);
-    // region shared by H (box-sum phase) and the block planes / TC copies
-    const int h_bytes = 2 * BR * p.h_pitch * 4;
-    const int p_bytes = up(nb * p.RGx * NP * 4, 16);
-    int tc_bytes = 0;
+    p.off_gst = take(nwin * ngr * 8);
     if (prec != PREC_FP32) {
-        p.tca_pitch = up(aw + 8, 8);
-        p.tcb_pitch = up(p.padl + aw + R + 1 + 16, 8);
+        const int MT = (8 + 2 * R + 15) / 16;
+        const int OFFB = p.padl - (R + 1);
+        p.tca_pitch = odd8(aw + 8);
+        p.tcb_pitch = odd8(OFFB + BC + 9);
         const int ta_rows = up(ah, 8) + 8;
-        const int ta_bytes = up(ta_rows * p.tca_pitch * 2, 16);
-        const int tb_bytes = up(2 * (BR + 32) * p.tcb_pitch * 2, 16);
-        const int sxc = ND < 9 ? ND : 9;
-        const int scr_bytes = (kThreads / 32) * sxc * ND * 8 * 4;
-        tc_bytes = ta_bytes + tb_bytes + scr_bytes;
-        p.off_h = off;
-        p.off_p = off;
-        p.off_tca = off + p_bytes;
-        p.off_tcb = p.off_tca + ta_bytes;
-        p.off_scr = p.off_tcb + tb_bytes;
-    } else {
-        p.off_h = off;
-        p.off_p = off;
+        const int tb_rows = std::max(BR, ah + 16 * MT) + 8;
+        p.off_tca = take(ta_rows * p.tca_pitch * 2);
+        p.off_tcb = take(2 * tb_rows * p.tcb_pitch * 2);
     }
-    off = up(off + std::max(h_bytes, p_bytes + tc_bytes), 16);
+    // region reused over the phases: C (box sums) -> P (block planes) + TC
+    // epilogue scratch -> P + per-window stencil buffers
+    const int c_bytes = 2 * vh * p.h_pitch * 4;
+    const int p_bytes = up(nb * p.RGx * NP * 4, 16);
+    const int sxc = ND < 3 ? ND : 3;
+    const int MT = (8 + 2 * R + 15) / 16;
+    const int scr_bytes = prec != PREC_FP32 ? up((kThreads / 32) * sxc * 16 * MT * 9 * 4, 16) : 0;
+    const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(nwin * ngr * 5 * 4, 16);
+    p.off_h = off;
+    p.off_p = off;
+    p.off_scr = off + p_bytes;
+    p.off_c5 = off + p_bytes;
+    p.off_peaks = p.off_c5 + up(nwin * 5 * 4, 16);
+    p.off_need = p.off_peaks + up(nwin * 4, 16);
+    p.off_dpart = p.off_need + up(nwin * 4, 16);
+    off = up(off + std::max(c_bytes, p_bytes + std::max(scr_bytes, win_bytes)), 16);
     p.smem_bytes = off;
-    p.max_windows = TX * TY;
+    p.max_windows = nwin;
     p.max_blocks = nb;
     Layout L;
     L.bytes = off;
@@ -146,7 +164,7 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan)
     for (int t = 8; t >= 1; --t) {
         const int TX = std::min(t, nx), TY = std::min(t, ny);
         Layout L = layout_for(TX, TY, w, s, R, G, prec);
-        if (L.bytes <= kSmemBudget || (t == 1 && L.bytes <= kSmemMax)) {
+        if (L.bytes <= smem_budget() || (t == 1 && L.bytes <= kSmemMax)) {
             *plan = L.p;
             plan->tiles_x = (nx + TX - 1) / TX;
             plan->tiles_y = (ny + TY - 1) / TY;

@@ -69,18 +69,18 @@ struct PassPlan {
     int RGx;  // partial planes per block
     // shared-memory layout (byte offsets) for a full tile
     int smem_bytes;
-    int off_nodes, node_cap;     // predictor nodes (u then v), node_cap floats each
-    int off_tabs;                // per-column / per-row grid weights
     int off_a, a_pitch;          // A - mu_T region, floats
     int off_b, b_pitch, padl;    // B' - mu_T region, floats; logical column 0 at padl - (R+1)
-    int off_h, h_pitch;          // H1 then H2 (row box sums), floats
-    int off_v;                   // V1 then V2 (window box sums), floats
+    int off_h, h_pitch;          // C1 then C2 (column box sums), floats; odd pitch >= BC
+    int off_v;                   // V1 then V2 (window box sums), same pitch
     int off_p;                   // block partial planes (aliases H)
     int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
     int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path), elements
     int off_scr;                 // TC epilogue scratch
     int off_stats;               // per-window mean / energy of A
     int off_red;                 // reduction scratch
+    int off_gst;                 // per-(window, 8-row group) sum and centred sum of squares of A
+    int off_c5, off_peaks, off_need, off_dpart;  // per-window stencil values, argmax, direct-sum mask and sums
     int max_windows, max_blocks;
 };
 
@@ -88,6 +88,10 @@ struct PassArgs {
     int W, H, fmt;
     long long pitch;       // bytes between image rows
     PtrRef img_a, img_b;
+    PtrRef bdef;           // warped frame B' (float, image grown by def_margin)
+    PtrRef adef;           // warped frame A' for the central warp (base null: A itself)
+    long long def_pitch;   // floats between rows of bdef / adef
+    int def_margin;
     int w, s, R, nx, ny;
     int deform;            // 0: frame B only, 1: central
     int prec;
@@ -96,6 +100,21 @@ struct PassArgs {
     PtrRef out_info;       // int32: bit0 valid, bits 8..15 ky, 16..23 kx
     PassPlan plan;
 };
+
+struct DeformArgs {
+    PtrRef img;
+    int fmt;
+    long long pitch;       // bytes between image rows
+    int W, H;
+    PtrRef pred_u, pred_v; // predictor grid (base null: zero displacement)
+    int w, s, nx, ny;
+    float scale;           // 1 (frame B), 0.5 / -0.5 (central warp of B / A)
+    int M;                 // margin of the output around the image
+    PtrRef out;            // float, (W + 2M) x (H + 2M), out_pitch floats per row
+    long long out_pitch;
+};
+cudaError_t launch_deform(const DeformArgs &a, int n_pairs, cudaStream_t st);
+bool deform_nodes_fit(int w, int s, int nx, int ny);
 
 // Returns false if (w, s, R, prec) is not supported by a compiled kernel.
 bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan);
