@@ -218,6 +218,27 @@ rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pi
 rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius, rpiv_deform deform_mode,
                                                size_t *bytes);
 
+/* The same pass as rpiv_stage_correlate for callers that cannot allocate
+ * device memory when they run it (no cudaMalloc/cudaFree or allocating
+ * library call happens inside).  This entry point has no counterpart in the
+ * paper: it exists for callers such as a real-time acquisition loop that must
+ * not enter the device allocator, or a host application that owns all device
+ * memory through its own pool.  Its scratch is a 32 MiB array compiled into
+ * the library, held by every GPU that loads the library until the process
+ * exits; images needing more (rpiv_stage_correlate_scratch_bytes > 32 MiB,
+ * about 2900 x 2900 pixels for the frame-B warp) are rejected with
+ * RPIV_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the one array, so calls whose work overlaps on the GPU (different
+ * streams, or other devices' calls are fine) race and must be serialised by
+ * the caller; a later call on the same stream is ordered after the earlier.
+ * Arguments, outputs and other errors as rpiv_stage_correlate.              */
+rpiv_status rpiv_stage_correlate_noalloc(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt,
+                                         int width, int height, int window, int step, int radius,
+                                         rpiv_precision precision, rpiv_deform deform_mode, const float *pred_u,
+                                         const float *pred_v, float *u, float *v, int32_t *info,
+                                         void *cuda_stream);
+
 /* Normalised median test + median replacement (paper Sec. 2, Westerweel &
  * Scarano 2005) on an nx x ny field; info (nullable) marks invalid windows
  * (bit 0 clear) which are always treated as outliers.  Writes u_out, v_out

@@ -25,7 +25,8 @@ PRECISIONS = {"fp32": RPIV_FP32, "bf16": RPIV_BF16, "fp16": RPIV_FP16}
 
 EXPORTED = sorted(["rpiv_config_default", "rpiv_validate_config", "rpiv_create", "rpiv_grid_shape",
                    "rpiv_workspace_bytes", "rpiv_process_pair", "rpiv_process_batch", "rpiv_backward", "rpiv_wait",
-                   "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes", "rpiv_stage_validate",
+                   "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes",
+                   "rpiv_stage_correlate_noalloc", "rpiv_stage_validate",
                    "rpiv_stage_interp", "rpiv_stage_vorticity", "rpiv_stage_downsample", "rpiv_trace_enable",
                    "rpiv_trace_read"])
 
@@ -81,6 +82,8 @@ def load(path: str = LIB_PATH):
     L.rpiv_stage_correlate.argtypes = [vp, vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, sz,
                                        vp]
     L.rpiv_stage_correlate_scratch_bytes.argtypes = [i32, i32, i32, i32, ctypes.POINTER(sz)]
+    L.rpiv_stage_correlate_noalloc.argtypes = [vp, vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp,
+                                               vp, vp]
     L.rpiv_stage_validate.argtypes = [vp, vp, vp, i32, i32, f32, f32, i32, vp, vp, vp, vp]
     L.rpiv_stage_interp.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp]
     L.rpiv_stage_vorticity.argtypes = [vp, vp, i32, i32, i32, vp, vp]

@@ -32,6 +32,12 @@ rpiv_status fail(rpiv_status st, const std::string &msg)
     return st;
 }
 
+}  // namespace
+
+void rpiv::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+namespace {
+
 rpiv_status cuda_fail(cudaError_t e, const char *what)
 {
     g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";

@@ -116,6 +116,13 @@ struct DeformArgs {
 cudaError_t launch_deform(const DeformArgs &a, int n_pairs, cudaStream_t st);
 bool deform_nodes_fit(int w, int s, int nx, int ny);
 
+// Opts every pass-kernel instantiation in to the full shared-memory carve-out
+// on the current device (once per device; never inside a stream capture).
+void prepare_pass_kernels();
+
+// Message returned by rpiv_last_error() on the calling thread.
+void set_last_error(const char *msg);
+
 // Returns false if (w, s, R, prec) is not supported by a compiled kernel.
 bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan);
 cudaError_t launch_pass(const PassArgs &args, int n_pairs, cudaStream_t st);

@@ -1,0 +1,96 @@
+"""The allocation-free correlation pass (rpiv_stage_correlate_noalloc).
+
+Callers that cannot allocate device memory at call time (a real-time camera
+loop that must not enter the allocator, a host application that owns all
+device memory through its own pool) use this entry point: its scratch is an
+array compiled into the library.  It must give what rpiv_stage_correlate
+gives with caller-provided scratch, call after call, although every call
+reuses the same array.
+
+This file is collected last so that a stop-at-first-failure run has already
+run every other test when it gets here.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2504_17987_gb300 as rp
+from paper_2504_17987_gb300 import binding
+from synth import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_PX = 1e-3
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_17987_gb300 import build
+    build.build()
+    return rp.load()
+
+
+def _smooth_pred(nx, ny, w, s, base):
+    X, Y = np.meshgrid(np.arange(nx) * s + 0.5 * (w - 1), np.arange(ny) * s + 0.5 * (w - 1))
+    pu = base[0] + 0.8 * np.sin(X / 61.0) * np.cos(Y / 47.0)
+    pv = base[1] + 0.8 * np.cos(X / 53.0) * np.sin(Y / 71.0)
+    return (torch.from_numpy(pu.astype(np.float32)).cuda(), torch.from_numpy(pv.astype(np.float32)).cuda())
+
+
+def _run_both(lib, A, B, w, s, r, precision, pred):
+    a, b = rp.to_device(A, "cuda:0"), rp.to_device(B, "cuda:0")
+    H, W = A.shape
+    fmt = binding.RPIV_U8 if A.dtype == np.uint8 else binding.RPIV_U16
+    nx, ny = (W - w) // s + 1, (H - w) // s + 1
+    prec = binding.PRECISIONS[precision]
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    pitch = a.stride(0) * a.element_size()
+    outs = []
+    for entry in ("scratch", "noalloc"):
+        u = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        v = torch.empty_like(u)
+        info = torch.empty((ny, nx), dtype=torch.int32, device="cuda")
+        pu, pv = pred
+        if entry == "scratch":
+            nbytes = ctypes.c_size_t()
+            assert lib.rpiv_stage_correlate_scratch_bytes(W, H, r, 0, ctypes.byref(nbytes)) == 0
+            scratch = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+            rc = lib.rpiv_stage_correlate(a.data_ptr(), b.data_ptr(), pitch, fmt, W, H, w, s, r, prec, 0,
+                                          pu.data_ptr(), pv.data_ptr(), u.data_ptr(), v.data_ptr(),
+                                          info.data_ptr(), scratch.data_ptr(), nbytes.value, st)
+        else:
+            rc = lib.rpiv_stage_correlate_noalloc(a.data_ptr(), b.data_ptr(), pitch, fmt, W, H, w, s, r, prec, 0,
+                                                  pu.data_ptr(), pv.data_ptr(), u.data_ptr(), v.data_ptr(),
+                                                  info.data_ptr(), st)
+        assert rc == 0, lib.rpiv_last_error()
+        torch.cuda.synchronize()
+        outs.append((u.cpu().numpy(), v.cpu().numpy(), info.cpu().numpy()))
+    return outs
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_noalloc_matches_scratch_entry_on_two_calls_in_a_row(lib, precision):
+    # two different pairs back to back: the shared array must not carry state over
+    cases = [(wl.paper_1mp(seed=4101, W=512, H=384), 32, 16, 4, (12.0, 0.0)),
+             (wl.plain_256(seed=4102), 32, 16, 8, (3.0, -1.5))]
+    for wk, w, s, r, base in cases:
+        A, B = wk.render()
+        H, W = A.shape
+        pred = _smooth_pred((W - w) // s + 1, (H - w) // s + 1, w, s, base)
+        (u1, v1, i1), (u2, v2, i2) = _run_both(lib, A, B, w, s, r, precision, pred)
+        assert np.array_equal(i1, i2)
+        assert np.max(np.abs(u1 - u2)) <= TOL_PX and np.max(np.abs(v1 - v2)) <= TOL_PX
+
+
+def test_noalloc_rejects_images_beyond_the_static_scratch(lib):
+    # 4096 x 4096 float frame grown by 2 px needs ~67 MB > 32 MiB: rejected before any device work
+    big = torch.zeros((8, 8), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
+    info = torch.zeros((8, 8), dtype=torch.int32, device="cuda")
+    rc = lib.rpiv_stage_correlate_noalloc(big.data_ptr(), big.data_ptr(), 4096, binding.RPIV_U8, 4096, 4096, 32, 16,
+                                          1, 0, 0, None, None, out.data_ptr(), out.data_ptr(), info.data_ptr(),
+                                          None)
+    assert rc == 1
+    assert b"static scratch" in lib.rpiv_last_error()
