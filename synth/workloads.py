@@ -134,3 +134,14 @@ def serving_stream_flow(stream: int, frame: int, W: int, H: int) -> Flow:
     xc = (x0 + 0.5 * frame) % W
     sign = 1.0 if rnd[2] < 0.5 else -1.0
     return Flow(U=4.0, V=0.0, vortices=[(xc, y0, sign * 200.0, 20.0)])
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> List[float]:
+    """Arrival times (s) of a Poisson process of the given rate: exponential
+    gaps by the inverse CDF of seeded uniforms."""
+    u = uniform(seed, n)
+    t, out = 0.0, []
+    for x in u:
+        t += -math.log(max(1.0 - float(x), 1e-300)) / rate
+        out.append(t)
+    return out
