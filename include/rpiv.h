@@ -204,9 +204,11 @@ const char *rpiv_last_error(void);
  *   info       ny x nx int32: bit 0 valid window, bits 8..15 the integer peak
  *              ky and bits 16..23 kx as int8.
  *   scratch    caller-owned device buffer of at least the size returned by
- *              rpiv_stage_correlate_scratch_bytes (the warped frame(s)); it
- *              must not be in use by other work on the device.
- * Errors: INVALID_ARG (sizes, nulls, radius, small scratch), UNSUPPORTED
+ *              rpiv_stage_correlate_scratch_bytes (frame A as float, or
+ *              the warped A' for the central warp, and the warped B'),
+ *              256-byte aligned; it must not be in use by other work on the
+ *              device.
+ * Errors: INVALID_ARG (sizes, nulls, radius, small or unaligned scratch), UNSUPPORTED
  * (precision not built for this radius or step), CUDA.                      */
 rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int width,
                                  int height, int window, int step, int radius, rpiv_precision precision,
@@ -214,7 +216,8 @@ rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pi
                                  float *v, int32_t *info, void *scratch, size_t scratch_bytes, void *cuda_stream);
 
 /* Scratch bytes rpiv_stage_correlate needs for a W x H image and radius r:
- * one float image grown by r + 1 pixels per side (two for the central warp). */
+ * two float images grown by M = r + 1 rounded up to a multiple of 4 pixels
+ * per side, rows padded to a multiple of 32 floats (either warp mode).      */
 rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius, rpiv_deform deform_mode,
                                                size_t *bytes);
 
@@ -226,7 +229,7 @@ rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius
  * memory through its own pool.  Its scratch is a 32 MiB array compiled into
  * the library, held by every GPU that loads the library until the process
  * exits; images needing more (rpiv_stage_correlate_scratch_bytes > 32 MiB,
- * about 2900 x 2900 pixels for the frame-B warp) are rejected with
+ * about 2000 x 2000 pixels) are rejected with
  * RPIV_ERR_INVALID_ARG.  The first call on a device looks up the array's
  * device address; make that first call before any stream capture.  All calls
  * share the one array, so calls whose work overlaps on the GPU (different

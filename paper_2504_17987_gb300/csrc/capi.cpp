@@ -72,6 +72,7 @@ struct StageDef {
     int w, s, R;
     int nx, ny;
     int prec;
+    long long fpitch;  // floats per row of this stage's frames (margin layout)
     size_t off_pred, off_raw, off_info, off_out, off_mask;  // per-pair workspace offsets
     PassPlan plan;
 };
@@ -158,11 +159,14 @@ struct rpiv_handle {
     rpiv_config cfg{};
     int device = 0;
     std::vector<StageDef> stages;
-    size_t pyr_off[RPIV_MAX_LEVELS + 1][2] = {};  // per-pair offsets of pyramid A/B images (level >= 1)
-    size_t def_off[2] = {};                       // per-pair offsets of the warped frames B' (and A')
-    int def_margin = 0;
-    long long def_pitch = 0;                      // floats per row of a warped frame
+    // per-pair offsets of the float frames (margin layout): [l][0] frame A at
+    // level l (level 0: ingested from the caller's image each call), [l][1]
+    // frame B at pyramid level l >= 1
+    size_t frame_off[RPIV_MAX_LEVELS + 1][2] = {};
+    size_t def_off[2] = {};  // per-pair offsets of the warped frames B' (and A')
+    int margin = 0;          // M of every frame
     size_t pair_stride = 0;
+    int *err_dev = nullptr;  // error word of the kernels' bounded waits
     char *ws = nullptr;
     size_t ws_bytes = 0;
     PairIO *io_dev = nullptr;
@@ -273,10 +277,16 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
     const int user_fmt = c.fmt == RPIV_U8 ? PIX_U8 : PIX_U16;
     const StageDef &p0 = h->stages[L];
     const bool run_pyr = L > 0 && any_nopred;
+    const bool central = c.deform_mode == RPIV_DEFORM_CENTRAL;
+    const int M = h->margin;
+    // byte offset of pixel (0, 0) inside a frame of the margin layout
+    auto interior = [&](long long fpitch) { return (size_t)((M * fpitch + M) * 4); };
 
-    auto run_pass = [&](const StageDef &d, PtrRef A, PtrRef B, int fmt, long long pch, bool pred) -> rpiv_status {
+    // A, B: the images the warp samples; afl: frame A of the margin layout
+    // (read by the pass when the first frame is not warped)
+    auto run_pass = [&](const StageDef &d, PtrRef A, PtrRef B, int fmt, long long pch, PtrRef afl,
+                        bool pred) -> rpiv_status {
         const size_t n1 = (size_t)d.nx * d.ny;
-        const bool central = c.deform_mode == RPIV_DEFORM_CENTRAL;
         for (int which = central ? 0 : 1; which < 2; ++which) {
             DeformArgs da;
             std::memset(&da, 0, sizeof(da));
@@ -292,19 +302,21 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
             da.nx = d.nx;
             da.ny = d.ny;
             da.scale = central ? (which ? 0.5f : -0.5f) : 1.0f;
-            da.M = h->def_margin;
+            da.M = M;
             da.out = ws(h->def_off[which]);
-            da.out_pitch = h->def_pitch;
+            da.out_pitch = d.fpitch;
             TraceScope ts(h, st, std::string(which ? "deform/" : "deformA/") + stage_tag(h, d),
                           geom_of(d.W, d.H, d.w, d.s, d.R, d.nx, d.ny, n));
             CK(launch_deform(da, n, st), "deformation launch");
         }
         PassArgs a;
         std::memset(&a, 0, sizeof(a));
+        a.afl = central ? ptr_direct(nullptr, 0) : afl;
         a.bdef = ws(h->def_off[1]);
         a.adef = central ? ws(h->def_off[0]) : ptr_direct(nullptr, 0);
-        a.def_pitch = h->def_pitch;
-        a.def_margin = h->def_margin;
+        a.def_pitch = d.fpitch;
+        a.def_margin = M;
+        a.err = h->err_dev;
         a.W = d.W;
         a.H = d.H;
         a.fmt = fmt;
@@ -378,8 +390,23 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
     rpiv_status rs;
 
     bool pass0_pred = false;
+    if (!central) {
+        // frame A as float, read by every full-resolution pass
+        IngestArgs ia;
+        ia.src = tab(&io[0].a);
+        ia.fmt = user_fmt;
+        ia.pitch = (long long)pitch;
+        ia.W = c.width;
+        ia.H = c.height;
+        ia.dst = ws(h->frame_off[0][0]);
+        ia.dst_pitch = p0.fpitch;
+        ia.dst_margin = M;
+        TraceScope ts(h, st, "ingest", geom_of(c.width, c.height, 0, 0, 0, 0, 0, n));
+        CK(launch_ingest(ia, n, st), "ingest launch");
+    }
     if (run_pyr) {
         for (int l = 1; l <= L; ++l) {
+            const StageDef &cur = h->stages[L - l];
             for (int ab = 0; ab < 2; ++ab) {
                 DownArgs d;
                 if (l == 1) {
@@ -390,13 +417,15 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
                     d.H = c.height;
                 } else {
                     const StageDef &prev = h->stages[L - (l - 1)];
-                    d.src = ws(h->pyr_off[l - 1][ab]);
+                    d.src = ws(h->frame_off[l - 1][ab] + interior(prev.fpitch));
                     d.fmt = PIX_F32;
-                    d.pitch = (long long)prev.W * 4;
+                    d.pitch = prev.fpitch * 4;
                     d.W = prev.W;
                     d.H = prev.H;
                 }
-                d.dst = ws(h->pyr_off[l][ab]);
+                d.dst = ws(h->frame_off[l][ab]);
+                d.dst_pitch = cur.fpitch;
+                d.dst_margin = M;
                 TraceScope ts(h, st, "down/L" + std::to_string(l), geom_of(d.W, d.H, 0, 0, 0, 0, 0, n));
                 CK(launch_down(d, n, st), "pyramid launch");
             }
@@ -409,8 +438,9 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
                 const size_t np = (size_t)prev.nx * prev.ny;
                 if ((rs = run_interp(prev, ws(prev.off_out), ws(prev.off_out + 4 * np), d, 1, 0)) != RPIV_OK) return rs;
             }
-            if ((rs = run_pass(d, ws(h->pyr_off[d.lvl][0]), ws(h->pyr_off[d.lvl][1]), PIX_F32, (long long)d.W * 4,
-                               pred)) != RPIV_OK)
+            const size_t in = interior(d.fpitch);
+            if ((rs = run_pass(d, ws(h->frame_off[d.lvl][0] + in), ws(h->frame_off[d.lvl][1] + in), PIX_F32,
+                               d.fpitch * 4, ws(h->frame_off[d.lvl][0]), pred)) != RPIV_OK)
                 return rs;
             if ((rs = run_uod(d, false)) != RPIV_OK) return rs;
         }
@@ -436,7 +466,9 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
             const size_t nprev = (size_t)prev.nx * prev.ny;
             if ((rs = run_interp(prev, ws(prev.off_out), ws(prev.off_out + 4 * nprev), d, 0, 0)) != RPIV_OK) return rs;
         }
-        if ((rs = run_pass(d, tab(&io[0].a), tab(&io[0].b), user_fmt, (long long)pitch, pred)) != RPIV_OK) return rs;
+        if ((rs = run_pass(d, tab(&io[0].a), tab(&io[0].b), user_fmt, (long long)pitch, ws(h->frame_off[0][0]),
+                           pred)) != RPIV_OK)
+            return rs;
         if ((rs = run_uod(d, p == np - 1)) != RPIV_OK) return rs;
         if (p < np - 1) {
             // the next pass reads this pass's validated field from the workspace
@@ -456,6 +488,109 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
 }
 
 }  // namespace
+
+// ------------------------------------------------ one pass on caller scratch --
+
+size_t rpiv::single_pass_scratch_bytes(int W, int H, int R)
+{
+    const int M = frame_margin(R);
+    return 2 * frame_bytes(W, H, M);  // frame A (or the warped A'), warped B'
+}
+
+int rpiv::single_pass(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int width, int height,
+                      int window, int step, int radius, int precision, int deform_mode, const float *pred_u,
+                      const float *pred_v, float *u, float *v, int32_t *info, void *scratch, cudaStream_t st)
+{
+    if (!img_a || !img_b || !u || !v || !info || !scratch) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if (reinterpret_cast<uintptr_t>(scratch) % 256)
+        return fail(RPIV_ERR_INVALID_ARG, "scratch must be 256-byte aligned");  // the pass copies 16-byte aligned rows
+    if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
+    if (fmt != 0 && fmt != RPIV_U8 && fmt != RPIV_U16) return fail(RPIV_ERR_INVALID_ARG, "fmt");
+    if (window < 2 || step < 1 || radius < 0 || radius > RPIV_MAX_RADIUS)
+        return fail(RPIV_ERR_INVALID_ARG, "window, step or radius out of range");
+    if (width > 65536 || height > 65536) return fail(RPIV_ERR_INVALID_ARG, "image size out of range");
+    if (width < window + 2 * (radius + 1) || height < window + 2 * (radius + 1))
+        return fail(RPIV_ERR_INVALID_ARG, "image smaller than window + 2 (radius + 1)");
+    const int bpp = fmt == RPIV_U8 ? 1 : (fmt == RPIV_U16 ? 2 : 4);
+    if (pitch_bytes < (size_t)width * bpp || pitch_bytes % bpp) return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes");
+    if (precision != RPIV_FP32 && precision != RPIV_BF16 && precision != RPIV_FP16)
+        return fail(RPIV_ERR_INVALID_ARG, "precision");
+    if (deform_mode != RPIV_DEFORM_B && deform_mode != RPIV_DEFORM_CENTRAL)
+        return fail(RPIV_ERR_INVALID_ARG, "deform_mode");
+    const int nx = grid_n(width, window, step), ny = grid_n(height, window, step);
+    if (!deform_nodes_fit(window, step, nx, ny)) return fail(RPIV_ERR_UNSUPPORTED, "step too small (minimum 3)");
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.prec = radius == 0 ? PREC_FP32 : prec_of((rpiv_precision)precision);
+    if (!pass_plan(window, step, radius, nx, ny, a.prec, &a.plan))
+        return fail(RPIV_ERR_UNSUPPORTED, "no kernel for this radius/precision/block size");
+    const int M = frame_margin(radius);
+    const long long fp = frame_pitch(width, M);
+    const size_t one = frame_bytes(width, height, M);
+    const bool central = deform_mode == RPIV_DEFORM_CENTRAL;
+    char *first = static_cast<char *>(scratch);  // frame A, or A' for the central warp
+    char *bdef = first + one;
+    const int pfmt = fmt == RPIV_U8 ? PIX_U8 : (fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
+    prepare_pass_kernels();
+    if (!central) {
+        IngestArgs ia;
+        ia.src = ptr_direct(img_a, 0);
+        ia.fmt = pfmt;
+        ia.pitch = (long long)pitch_bytes;
+        ia.W = width;
+        ia.H = height;
+        ia.dst = ptr_direct(first, 0);
+        ia.dst_pitch = fp;
+        ia.dst_margin = M;
+        CK(launch_ingest(ia, 1, st), "ingest launch");
+    }
+    for (int which = central ? 0 : 1; which < 2; ++which) {
+        DeformArgs da;
+        std::memset(&da, 0, sizeof(da));
+        da.img = ptr_direct(which ? img_b : img_a, 0);
+        da.fmt = pfmt;
+        da.pitch = (long long)pitch_bytes;
+        da.W = width;
+        da.H = height;
+        da.pred_u = ptr_direct(pred_u, 0);
+        da.pred_v = ptr_direct(pred_v, 0);
+        da.w = window;
+        da.s = step;
+        da.nx = nx;
+        da.ny = ny;
+        da.scale = central ? (which ? 0.5f : -0.5f) : 1.0f;
+        da.M = M;
+        da.out = ptr_direct(which ? bdef : first, 0);
+        da.out_pitch = fp;
+        CK(launch_deform(da, 1, st), "deformation launch");
+    }
+    a.W = width;
+    a.H = height;
+    a.fmt = pfmt;
+    a.pitch = (long long)pitch_bytes;
+    a.img_a = ptr_direct(img_a, 0);
+    a.img_b = ptr_direct(img_b, 0);
+    a.afl = ptr_direct(central ? nullptr : first, 0);
+    a.bdef = ptr_direct(bdef, 0);
+    a.adef = ptr_direct(central ? first : nullptr, 0);
+    a.def_pitch = fp;
+    a.def_margin = M;
+    a.err = nullptr;
+    a.w = window;
+    a.s = step;
+    a.R = radius;
+    a.nx = nx;
+    a.ny = ny;
+    a.deform = central ? 1 : 0;
+    a.pred_u = ptr_direct(pred_u, 0);
+    a.pred_v = ptr_direct(pred_v, 0);
+    a.out_u = ptr_direct(u, 0);
+    a.out_v = ptr_direct(v, 0);
+    a.out_info = ptr_direct(info, 0);
+    CK(launch_pass(a, 1, st), "correlation pass launch");
+    g_err.clear();
+    return RPIV_OK;
+}
 
 // ===================================================================== ABI ==
 
@@ -523,22 +658,23 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
         return o;
     };
     {
+        int Rmax = 0;
+        for (auto &d : h->stages) Rmax = std::max(Rmax, d.R);
+        const int M = frame_margin(Rmax);
+        h->margin = M;
+        for (auto &d : h->stages) d.fpitch = frame_pitch(d.W, M);
+        const bool central = cfg->deform_mode == RPIV_DEFORM_CENTRAL;
+        if (!central) h->frame_off[0][0] = take(frame_bytes(cfg->width, cfg->height, M));
         int W = cfg->width, H = cfg->height;
         for (int l = 1; l <= cfg->predictor_levels; ++l) {
             W /= 2;
             H /= 2;
-            h->pyr_off[l][0] = take((size_t)W * H * 4);
-            h->pyr_off[l][1] = take((size_t)W * H * 4);
+            h->frame_off[l][0] = take(frame_bytes(W, H, M));
+            h->frame_off[l][1] = take(frame_bytes(W, H, M));
         }
-    }
-    {
-        int M = 0;
-        for (auto &d : h->stages) M = std::max(M, d.R + 1);
-        h->def_margin = M;
-        h->def_pitch = (long long)up((size_t)cfg->width + 2 * M, 32);
-        const size_t bytes = (size_t)h->def_pitch * (cfg->height + 2 * M) * 4;
-        h->def_off[1] = take(bytes);
-        if (cfg->deform_mode == RPIV_DEFORM_CENTRAL) h->def_off[0] = take(bytes);
+        // the warped frames of the largest stage serve every stage
+        h->def_off[1] = take(frame_bytes(cfg->width, cfg->height, M));
+        if (central) h->def_off[0] = take(frame_bytes(cfg->width, cfg->height, M));
     }
     for (auto &d : h->stages) {
         const size_t n1 = (size_t)d.nx * d.ny;
@@ -564,6 +700,12 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
         cudaGetLastError();
         return cleanup(RPIV_ERR_OOM, "pointer table allocation failed");
     }
+    e = cudaMalloc(&h->err_dev, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(RPIV_ERR_OOM, "error word allocation failed");
+    }
+    if ((e = cudaMemset(h->err_dev, 0, sizeof(int))) != cudaSuccess) return cleanup(RPIV_ERR_CUDA, "error word reset failed");
     e = cudaHostAlloc(&h->ring, sizeof(PairIO) * cfg->max_batch * kRing, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -753,7 +895,20 @@ rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms)
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         const cudaError_t e = cudaEventQuery(h->done_ev);
-        if (e == cudaSuccess) return RPIV_OK;
+        if (e == cudaSuccess) {
+            // a kernel whose bounded wait gave up reported its tiles invalid and set the word
+            int err = 0;
+            cudaError_t e2 = cudaMemcpyAsync(&err, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->cap_stream);
+            if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->cap_stream);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "error word read");
+            if (err) {
+                cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->cap_stream);
+                cudaStreamSynchronize(h->cap_stream);
+                return fail(RPIV_ERR_TIMEOUT, "a tile's region load did not complete within its bounded wait; "
+                                              "its windows were reported invalid");
+            }
+            return RPIV_OK;
+        }
         if (e != cudaErrorNotReady) return cuda_fail(e, "event query");
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
         if (ms.count() >= timeout_ms) return fail(RPIV_ERR_TIMEOUT, "work did not finish within the timeout");
@@ -816,6 +971,7 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
         if (h->done_ev) cudaEventDestroy(h->done_ev);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         if (h->ws) cudaFree(h->ws);
+        if (h->err_dev) cudaFree(h->err_dev);
         if (h->io_dev) cudaFree(h->io_dev);
         if (h->ring) cudaFreeHost(h->ring);
         if (h->adj_ws) cudaFree(h->adj_ws);
@@ -827,22 +983,15 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
 
 // -------------------------------------------------------- stage entries --
 
-static void stage_def_geom(int width, int height, int radius, long long *pitch, size_t *one)
-{
-    const int M = radius + 1;
-    *pitch = (long long)up((size_t)width + 2 * M, 32);
-    *one = (size_t)(*pitch) * (height + 2 * M) * 4;
-}
-
 rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius, rpiv_deform deform_mode,
                                                size_t *bytes)
 {
-    if (!bytes || width < 1 || height < 1 || radius < 0 || radius > RPIV_MAX_RADIUS)
+    if (!bytes || width < 1 || height < 1 || width > 65536 || height > 65536 || radius < 0 ||
+        radius > RPIV_MAX_RADIUS)
         return fail(RPIV_ERR_INVALID_ARG, "bad argument");
-    long long pitch;
-    size_t one;
-    stage_def_geom(width, height, radius, &pitch, &one);
-    *bytes = up(one, 256) * (deform_mode == RPIV_DEFORM_CENTRAL ? 2 : 1);
+    if (deform_mode != RPIV_DEFORM_B && deform_mode != RPIV_DEFORM_CENTRAL)
+        return fail(RPIV_ERR_INVALID_ARG, "deform_mode");
+    *bytes = single_pass_scratch_bytes(width, height, radius);
     return RPIV_OK;
 }
 
@@ -851,80 +1000,14 @@ rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pi
                                  rpiv_deform deform_mode, const float *pred_u, const float *pred_v, float *u,
                                  float *v, int32_t *info, void *scratch, size_t scratch_bytes, void *cuda_stream)
 {
-    if (!img_a || !img_b || !u || !v || !info || !scratch) return fail(RPIV_ERR_INVALID_ARG, "null argument");
-    if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
-    if (fmt != 0 && fmt != RPIV_U8 && fmt != RPIV_U16) return fail(RPIV_ERR_INVALID_ARG, "fmt");
-    if (window < 2 || step < 1 || radius < 0 || radius > RPIV_MAX_RADIUS)
-        return fail(RPIV_ERR_INVALID_ARG, "window, step or radius out of range");
-    if (width < window + 2 * (radius + 1) || height < window + 2 * (radius + 1))
-        return fail(RPIV_ERR_INVALID_ARG, "image smaller than window + 2 (radius + 1)");
-    const int bpp = fmt == RPIV_U8 ? 1 : (fmt == RPIV_U16 ? 2 : 4);
-    if (pitch_bytes < (size_t)width * bpp || pitch_bytes % bpp) return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes");
-    if (precision != RPIV_FP32 && precision != RPIV_BF16 && precision != RPIV_FP16)
-        return fail(RPIV_ERR_INVALID_ARG, "precision");
-    if (deform_mode != RPIV_DEFORM_B && deform_mode != RPIV_DEFORM_CENTRAL)
-        return fail(RPIV_ERR_INVALID_ARG, "deform_mode");
-    size_t need = 0;
-    rpiv_stage_correlate_scratch_bytes(width, height, radius, deform_mode, &need);
-    if (scratch_bytes < need) return fail(RPIV_ERR_INVALID_ARG, "scratch smaller than rpiv_stage_correlate_scratch_bytes");
-    const int nx = grid_n(width, window, step), ny = grid_n(height, window, step);
-    if (!deform_nodes_fit(window, step, nx, ny)) return fail(RPIV_ERR_UNSUPPORTED, "step too small (minimum 3)");
-    PassArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.prec = radius == 0 ? PREC_FP32 : prec_of(precision);
-    if (!pass_plan(window, step, radius, nx, ny, a.prec, &a.plan))
-        return fail(RPIV_ERR_UNSUPPORTED, "no kernel for this radius/precision/block size");
-    long long dpitch;
-    size_t one;
-    stage_def_geom(width, height, radius, &dpitch, &one);
-    char *bdef = static_cast<char *>(scratch);
-    char *adef = deform_mode == RPIV_DEFORM_CENTRAL ? bdef + up(one, 256) : nullptr;
-    const int pfmt = fmt == RPIV_U8 ? PIX_U8 : (fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    prepare_pass_kernels();
-    for (int which = adef ? 0 : 1; which < 2; ++which) {
-        DeformArgs da;
-        std::memset(&da, 0, sizeof(da));
-        da.img = ptr_direct(which ? img_b : img_a, 0);
-        da.fmt = pfmt;
-        da.pitch = (long long)pitch_bytes;
-        da.W = width;
-        da.H = height;
-        da.pred_u = ptr_direct(pred_u, 0);
-        da.pred_v = ptr_direct(pred_v, 0);
-        da.w = window;
-        da.s = step;
-        da.nx = nx;
-        da.ny = ny;
-        da.scale = adef ? (which ? 0.5f : -0.5f) : 1.0f;
-        da.M = radius + 1;
-        da.out = ptr_direct(which ? bdef : adef, 0);
-        da.out_pitch = dpitch;
-        CK(launch_deform(da, 1, st), "deformation launch");
-    }
-    a.W = width;
-    a.H = height;
-    a.fmt = pfmt;
-    a.pitch = (long long)pitch_bytes;
-    a.img_a = ptr_direct(img_a, 0);
-    a.img_b = ptr_direct(img_b, 0);
-    a.bdef = ptr_direct(bdef, 0);
-    a.adef = ptr_direct(adef, 0);
-    a.def_pitch = dpitch;
-    a.def_margin = radius + 1;
-    a.w = window;
-    a.s = step;
-    a.R = radius;
-    a.nx = nx;
-    a.ny = ny;
-    a.deform = adef ? 1 : 0;
-    a.pred_u = ptr_direct(pred_u, 0);
-    a.pred_v = ptr_direct(pred_v, 0);
-    a.out_u = ptr_direct(u, 0);
-    a.out_v = ptr_direct(v, 0);
-    a.out_info = ptr_direct(info, 0);
-    CK(launch_pass(a, 1, st), "correlation pass launch");
-    return RPIV_OK;
+    if (!scratch) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if (width < 1 || height < 1 || width > 65536 || height > 65536 || radius < 0 || radius > RPIV_MAX_RADIUS)
+        return fail(RPIV_ERR_INVALID_ARG, "image size or radius out of range");
+    if (scratch_bytes < single_pass_scratch_bytes(width, height, radius))
+        return fail(RPIV_ERR_INVALID_ARG, "scratch smaller than rpiv_stage_correlate_scratch_bytes");
+    return (rpiv_status)single_pass(img_a, img_b, pitch_bytes, fmt, width, height, window, step, radius,
+                                    (int)precision, (int)deform_mode, pred_u, pred_v, u, v, info, scratch,
+                                    static_cast<cudaStream_t>(cuda_stream));
 }
 
 rpiv_status rpiv_stage_validate(const float *u, const float *v, const int32_t *info, int nx, int ny, float threshold,
@@ -1002,6 +1085,8 @@ rpiv_status rpiv_stage_downsample(const void *img, size_t pitch_bytes, int fmt, 
     a.W = width;
     a.H = height;
     a.dst = ptr_direct(out, 0);
+    a.dst_pitch = width / 2;
+    a.dst_margin = 0;
     CK(launch_down(a, 1, static_cast<cudaStream_t>(cuda_stream)), "downsample launch");
     return RPIV_OK;
 }

@@ -308,7 +308,28 @@ __global__ void down_kernel(const DownArgs a)
     if (a.fmt == PIX_U8) val = box2<uint8_t>(src, a.pitch, x, y);
     else if (a.fmt == PIX_U16) val = box2<uint16_t>(src, a.pitch, x, y);
     else val = box2<float>(src, a.pitch, x, y);
-    dst[(long long)y * W2 + x] = val;
+    dst[(long long)(y + a.dst_margin) * a.dst_pitch + (x + a.dst_margin)] = val;
+}
+
+__global__ void ingest_kernel(const IngestArgs a)
+{
+    const int pair = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const unsigned char *src = (const unsigned char *)resolve(a.src, pair);
+    float *dst = (float *)resolve(a.dst, pair);
+    float val;
+    if (a.fmt == PIX_U8) val = ldp<uint8_t>(src, a.pitch, x, y);
+    else if (a.fmt == PIX_U16) val = ldp<uint16_t>(src, a.pitch, x, y);
+    else val = ldp<float>(src, a.pitch, x, y);
+    dst[(long long)(y + a.dst_margin) * a.dst_pitch + (x + a.dst_margin)] = val;
+}
+
+cudaError_t launch_ingest(const IngestArgs &a, int n_pairs, cudaStream_t st)
+{
+    dim3 grid((a.W + 255) / 256, a.H, n_pairs);
+    ingest_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_down(const DownArgs &a, int n_pairs, cudaStream_t st)

@@ -95,67 +95,113 @@ __host__ __device__ inline int tc_b_rows(int BR, int ah, int R)
 
 // ------------------------------------------------------- region loads --
 
-// A region (raw image, or the central-warped frame A'), tile mean mu_T,
-// centred A and B' regions in FP32, and for the tensor-core path their
-// 16-bit copies (B' twice, the second shifted one column left, so that every
-// column pair starts 4-byte aligned).
-template <typename T, int PREC>
-__device__ void load_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs, uint16_t *TA,
-                             uint16_t *TB, float *red)
+constexpr int MBAR_SPIN_LIMIT = 1 << 22;  // bounded wait for the bulk copies
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// one contiguous global -> shared copy (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ int up4(int x) { return (x + 3) & ~3; }
+
+// A region (raw frame A, or the central-warped A') and B' region, raw values,
+// from the float frames in the workspace (margin layout).  With a step that is
+// a multiple of 4 every row is one 16-byte-aligned bulk copy completing on an
+// mbarrier (bounded wait: on timeout the error word is set and false returned);
+// otherwise plain loads.
+static __device__ bool load_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs,
+                                    uint64_t *bar)
+{
+    const PassPlan &P = a.plan;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const float *asrc = (const float *)resolve(a.adef.base ? a.adef : a.afl, pair);
+    const float *bsrc = (const float *)resolve(a.bdef, pair);
+    const long long dp = a.def_pitch;
+    const int M = a.def_margin;
+    const float *a0 = asrc + (long long)(g.ay0 + M) * dp + (g.ax0 + M);
+    if (a.s % 4 == 0) {
+        // B' rows start at smem column 0, i.e. global column ax0 + M - padl
+        const float *b0 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 + M - P.padl);
+        const int acols = up4(g.aw), bcols = up4(g.OFFB + g.BC);
+        const uint32_t bytes = (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            fence_proxy_async();
+        }
+        __syncthreads();
+        if (tid < 32) {
+            if (lane == 0) mbar_expect_tx(bar, bytes);
+            __syncwarp();
+            for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
+            for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
+        }
+        for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+            if (mbar_try_wait(bar, 0)) return true;
+        if (a.err) atomicOr(a.err, 1);
+        // give copies still in flight a bounded chance to land before the CTA exits
+        for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+            if (mbar_try_wait(bar, 0)) break;
+        return false;
+    }
+    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next())
+        As[it.y * P.a_pitch + it.x] = a0[(long long)it.y * dp + it.x];
+    const float *b1 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 - (g.R + 1) + M);
+    for (Walk2D it(tid, blockDim.x, g.BC); it.y < g.BR; it.next())
+        Bs[it.y * P.b_pitch + g.OFFB + it.x] = b1[(long long)it.y * dp + it.x];
+    return true;
+}
+
+// 16-bit copies for the tensor-core path: A, and B' twice (the second shifted
+// one column left so that every column pair starts 4-byte aligned), with zeros
+// wherever fragments may reach outside the staged region.
+template <int PREC>
+__device__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, uint16_t *TA,
+                          uint16_t *TB)
 {
     const PassPlan &P = a.plan;
     const int tid = threadIdx.x;
-    const int R = g.R;
-    const float *adef = (const float *)resolve(a.adef, pair);
-    const float *bdef = (const float *)resolve(a.bdef, pair);
-    const unsigned char *imgA = (const unsigned char *)resolve(a.img_a, pair);
-    const long long dp = a.def_pitch;
-    const int M = a.def_margin;
-    float local = 0.f;
-    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next()) {
-        const int x = g.ax0 + it.x, y = g.ay0 + it.y;
-        const float v = adef ? adef[(long long)(y + M) * dp + (x + M)] : ld_px<T>(imgA, a.pitch, x, y);
-        As[it.y * P.a_pitch + it.x] = v;
-        local += v;
-    }
-    local = warp_sum(local);
-    if ((tid & 31) == 0) red[tid >> 5] = local;
-    __syncthreads();
-    if (tid < 32) {
-        float v = tid < (int)(blockDim.x >> 5) ? red[tid] : 0.f;
-        v = warp_sum(v);
-        if (tid == 0) red[32] = v / (float)(g.aw * g.ah);
-    }
-    __syncthreads();
-    const float muT = red[32];
-    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next()) {
-        const float v = As[it.y * P.a_pitch + it.x] - muT;
-        As[it.y * P.a_pitch + it.x] = v;
-        if (PREC != PREC_FP32) TA[it.y * P.tca_pitch + it.x] = to_h16<PREC>(v);
-    }
-    const int brows = tc_b_rows(g.BR, g.ah, R);
+    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next())
+        TA[it.y * P.tca_pitch + it.x] = to_h16<PREC>(As[it.y * P.a_pitch + it.x]);
+    const int brows = tc_b_rows(g.BR, g.ah, g.R);
     uint16_t *TB1 = TB + brows * P.tcb_pitch;
-    const float *src = bdef + (long long)(g.ay0 - (R + 1) + M) * dp + (g.ax0 - (R + 1) + M);
-    for (Walk2D it(tid, blockDim.x, g.BC); it.y < g.BR; it.next()) {
-        const float v = src[(long long)it.y * dp + it.x] - muT;
-        Bs[it.y * P.b_pitch + g.OFFB + it.x] = v;
-        if (PREC != PREC_FP32) {
-            const uint16_t h = to_h16<PREC>(v);
-            TB[it.y * P.tcb_pitch + g.OFFB + it.x] = h;
-            if (g.OFFB + it.x >= 1) TB1[it.y * P.tcb_pitch + g.OFFB + it.x - 1] = h;
-        }
-    }
-    if (PREC != PREC_FP32) {
-        // zero the part of the copies that fragments may touch outside the region
-        const int c_lo = g.OFFB + g.BC - 1, c_n = 9;
-        for (Walk2D it(tid, blockDim.x, c_n); it.y < g.BR; it.next()) {
-            if (it.x > 0) TB[it.y * P.tcb_pitch + c_lo + it.x] = 0;
-            TB1[it.y * P.tcb_pitch + c_lo + it.x] = 0;
-        }
-        for (Walk2D it(tid, blockDim.x, P.tcb_pitch); it.y < brows - g.BR; it.next()) {
-            TB[(g.BR + it.y) * P.tcb_pitch + it.x] = 0;
-            TB1[(g.BR + it.y) * P.tcb_pitch + it.x] = 0;
-        }
+    const int lo = g.OFFB, hi = g.OFFB + g.BC;  // staged columns
+    const int cols = hi + 8;                     // fragments reach at most 8 columns past the region
+    for (Walk2D it(tid, blockDim.x, cols); it.y < brows; it.next()) {
+        const int y = it.y, x = it.x;
+        const bool row_ok = y < g.BR;
+        const float v0 = (row_ok && x >= lo && x < hi) ? Bs[y * P.b_pitch + x] : 0.f;
+        const float v1 = (row_ok && x + 1 >= lo && x + 1 < hi) ? Bs[y * P.b_pitch + x + 1] : 0.f;
+        TB[y * P.tcb_pitch + x] = to_h16<PREC>(v0);
+        TB1[y * P.tcb_pitch + x] = to_h16<PREC>(v1);
     }
 }
 
@@ -216,48 +262,52 @@ static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const floa
     }
 }
 
-// Sum and centred sum of squares of every 8-row group of every A window; one
-// warp per (window, group), lanes along the columns, two passes.
-static __device__ void window_group_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *gst)
+// Sum and centred sum of squares of every G x G block of A (two passes; one
+// warp per block, lanes along the rows): bst[b] = (sum, M2).
+static __device__ void block_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int w = a.w, ngr = (w + 7) / 8;
-    for (int it = warp; it < g.nwin * ngr; it += nwarps) {
-        const int wi = it / ngr, gr = it - wi * ngr;
-        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
-        const int rows = min(8, w - 8 * gr);
-        const float *base = As + (wyi * a.s + 8 * gr) * P.a_pitch + wxi * a.s;
+    const int G = P.G;
+    const float n = (float)(G * G);
+    for (int b = warp; b < g.nb; b += nwarps) {
+        const int bxi = b % g.nbx, byi = b / g.nbx;
+        const float *base = As + (byi * G) * P.a_pitch + bxi * G;
         float s = 0.f;
-        for (Walk2D e(lane, 32, w); e.y < rows; e.next()) s += base[e.y * P.a_pitch + e.x];
+        for (Walk2D e(lane, 32, G); e.y < G; e.next()) s += base[e.y * P.a_pitch + e.x];
         s = warp_sum(s);
-        const float m = s / (float)(rows * w);
+        const float m = s / n;
         float q = 0.f;
-        for (Walk2D e(lane, 32, w); e.y < rows; e.next()) {
+        for (Walk2D e(lane, 32, G); e.y < G; e.next()) {
             const float d = base[e.y * P.a_pitch + e.x] - m;
             q = fmaf(d, d, q);
         }
         q = warp_sum(q);
-        if (lane == 0) gst[it] = make_float2(s, q);
+        if (lane == 0) bst[b] = make_float2(s, q);
     }
 }
 
-// Window mean and energy from its groups: E = sum M2_g + sum n_g (mean_g - mean)^2.
-static __device__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *gst, float *stats)
+// Window mean and energy from its blocks (parallel-variance identity):
+// E = sum M2_b + n_b sum (mean_b - mean)^2, in a fixed order.
+static __device__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *bst, float *stats)
 {
-    const int w = a.w, ngr = (w + 7) / 8;
-    const float n = (float)(w * w);
+    const PassPlan &P = a.plan;
+    const int G = P.G, kb = a.w / G;
+    const float nb = (float)(G * G), n = (float)(a.w * a.w);
     for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
+        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
+        const int bx0 = (wxi * a.s) / G, by0 = (wyi * a.s) / G;
         float s = 0.f;
-        for (int gr = 0; gr < ngr; ++gr) s += gst[wi * ngr + gr].x;
+        for (int yy = 0; yy < kb; ++yy)
+            for (int xx = 0; xx < kb; ++xx) s += bst[(by0 + yy) * g.nbx + bx0 + xx].x;
         const float mean = s / n;
         float e = 0.f;
-        for (int gr = 0; gr < ngr; ++gr) {
-            const float ng = (float)(min(8, w - 8 * gr) * w);
-            const float2 p = gst[wi * ngr + gr];
-            const float d = p.x / ng - mean;
-            e += p.y + ng * d * d;
-        }
+        for (int yy = 0; yy < kb; ++yy)
+            for (int xx = 0; xx < kb; ++xx) {
+                const float2 p = bst[(by0 + yy) * g.nbx + bx0 + xx];
+                const float d = p.x / nb - mean;
+                e += p.y + nb * d * d;
+            }
         stats[2 * wi] = mean;
         stats[2 * wi + 1] = e;
     }
@@ -676,6 +726,24 @@ static __device__ void finalize(const PassArgs &a, const TileGeom &g, const floa
     }
 }
 
+// A tile whose region load did not complete: its windows are reported
+// invalid (the predictor passes through, info 0), as for a degenerate window,
+// so that the outlier test replaces them; the error word carries the event.
+static __device__ void invalid_tile(const PassArgs &a, const TileGeom &g, int pair)
+{
+    const float *pu = (const float *)resolve(a.pred_u, pair);
+    const float *pv = (const float *)resolve(a.pred_v, pair);
+    float *ou = (float *)resolve(a.out_u, pair);
+    float *ov = (float *)resolve(a.out_v, pair);
+    int32_t *oi = (int32_t *)resolve(a.out_info, pair);
+    for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
+        const int k = (g.wy0 + wi / g.nwx) * a.nx + (g.wx0 + wi % g.nwx);
+        ou[k] = pu ? pu[k] : 0.f;
+        ov[k] = pv ? pv[k] : 0.f;
+        oi[k] = 0;
+    }
+}
+
 // ------------------------------------------------------------- the kernel --
 
 template <int RC, int PREC>
@@ -713,8 +781,8 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
     float *Vs = reinterpret_cast<float *>(smem + P.off_v);
     float *Ps = reinterpret_cast<float *>(smem + P.off_p);
     float *stats = reinterpret_cast<float *>(smem + P.off_stats);
-    float *red = reinterpret_cast<float *>(smem + P.off_red);
-    float2 *gst = reinterpret_cast<float2 *>(smem + P.off_gst);
+    float2 *bst = reinterpret_cast<float2 *>(smem + P.off_gst);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + P.off_red);
     uint16_t *TA = reinterpret_cast<uint16_t *>(smem + P.off_tca);
     uint16_t *TB = reinterpret_cast<uint16_t *>(smem + P.off_tcb);
     WinShared ws;
@@ -724,19 +792,19 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
     ws.dpart = reinterpret_cast<float *>(smem + P.off_dpart);
 
     // 1: A and B' regions (and their 16-bit copies on the tensor-core path)
-    if (a.fmt == PIX_U8)
-        load_regions<uint8_t, PREC>(a, g, pair, As, Bs, TA, TB, red);
-    else if (a.fmt == PIX_U16)
-        load_regions<uint16_t, PREC>(a, g, pair, As, Bs, TA, TB, red);
-    else
-        load_regions<float, PREC>(a, g, pair, As, Bs, TA, TB, red);
-    __syncthreads();
+    // every thread leaves together if any thread's bounded wait gave up (error word set)
+    const bool loaded = load_regions(a, g, pair, As, Bs, bar);
+    if (__syncthreads_or(!loaded)) {
+        invalid_tile(a, g, pair);
+        return;
+    }
+    if (PREC != PREC_FP32) tc_copies<PREC>(a, g, As, Bs, TA, TB);
 
     // 2: A window statistics, box sums of B' for every window and shift
-    window_group_stats(a, g, As, gst);
+    block_stats(a, g, As, bst);
     box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
     __syncthreads();
-    window_stats(a, g, gst, stats);
+    window_stats(a, g, bst, stats);
 
     // 3: block partial planes (alias the dead C region)
     if (PREC == PREC_FP32) {

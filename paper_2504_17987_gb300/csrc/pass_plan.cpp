@@ -32,16 +32,19 @@ void prepare_pass_kernels()
 namespace {
 
 constexpr int kThreads = 256;
-// Shared memory a tile may use: 112 KB keeps two CTAs per SM (228 KB per SM,
-// 1 KB reserved per CTA).  RPIV_TILE_SMEM_KB overrides it (tuning).
-int smem_budget()
+// Shared memory a tile may use (228 KB per SM, 1 KB reserved per CTA).  The
+// FP32 kernel runs best at about four CTAs per SM (56 KB), the tensor-core
+// kernel, whose 16-bit copies double the staged bytes, at two (112 KB); both
+// measured on GB300 over 40..112 KB.  RPIV_TILE_SMEM_KB overrides it (tuning).
+int smem_budget(int prec)
 {
     static int kb = [] {
         const char *e = std::getenv("RPIV_TILE_SMEM_KB");
         const int v = e ? std::atoi(e) : 0;
-        return (v >= 16 && v <= 227) ? v : 112;
+        return (v >= 16 && v <= 227) ? v : 0;
     }();
-    return kb * 1024;
+    if (kb) return kb * 1024;
+    return (prec == PREC_FP32 ? 56 : 112) * 1024;
 }
 constexpr int kSmemMax = 227 * 1024;
 
@@ -108,8 +111,8 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     p.off_b = take(BR * p.b_pitch * 4);
     p.off_v = take(2 * vh * p.h_pitch * 4);
     p.off_stats = take(2 * nwin * 4);
-    p.off_red = take(40 * 4);
-    p.off_gst = take(nwin * ngr * 8);
+    p.off_red = take(16);      // the region loads' mbarrier
+    p.off_gst = take(nb * 8);  // per-block (sum, centred sum of squares) of A
     if (prec != PREC_FP32) {
         const int MT = (8 + 2 * R + 15) / 16;
         const int OFFB = p.padl - (R + 1);
@@ -164,7 +167,7 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan)
     for (int t = 8; t >= 1; --t) {
         const int TX = std::min(t, nx), TY = std::min(t, ny);
         Layout L = layout_for(TX, TY, w, s, R, G, prec);
-        if (L.bytes <= smem_budget() || (t == 1 && L.bytes <= kSmemMax)) {
+        if (L.bytes <= smem_budget(prec) || (t == 1 && L.bytes <= kSmemMax)) {
             *plan = L.p;
             plan->tiles_x = (nx + TX - 1) / TX;
             plan->tiles_y = (ny + TY - 1) / TY;

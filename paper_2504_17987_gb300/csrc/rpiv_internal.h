@@ -69,8 +69,8 @@ struct PassPlan {
     int RGx;  // partial planes per block
     // shared-memory layout (byte offsets) for a full tile
     int smem_bytes;
-    int off_a, a_pitch;          // A - mu_T region, floats
-    int off_b, b_pitch, padl;    // B' - mu_T region, floats; logical column 0 at padl - (R+1)
+    int off_a, a_pitch;          // A region, floats
+    int off_b, b_pitch, padl;    // B' region, floats; logical column 0 at padl - (R+1)
     int off_h, h_pitch;          // C1 then C2 (column box sums), floats; odd pitch >= BC
     int off_v;                   // V1 then V2 (window box sums), same pitch
     int off_p;                   // block partial planes (aliases H)
@@ -78,8 +78,8 @@ struct PassPlan {
     int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path), elements
     int off_scr;                 // TC epilogue scratch
     int off_stats;               // per-window mean / energy of A
-    int off_red;                 // reduction scratch
-    int off_gst;                 // per-(window, 8-row group) sum and centred sum of squares of A
+    int off_red;                 // mbarrier of the bulk region loads
+    int off_gst;                 // per-G x G block sum and centred sum of squares of A
     int off_c5, off_peaks, off_need, off_dpart;  // per-window stencil values, argmax, direct-sum mask and sums
     int max_windows, max_blocks;
 };
@@ -88,10 +88,12 @@ struct PassArgs {
     int W, H, fmt;
     long long pitch;       // bytes between image rows
     PtrRef img_a, img_b;
+    PtrRef afl;            // frame A as float (image grown by def_margin, interior written)
     PtrRef bdef;           // warped frame B' (float, image grown by def_margin)
-    PtrRef adef;           // warped frame A' for the central warp (base null: A itself)
-    long long def_pitch;   // floats between rows of bdef / adef
-    int def_margin;
+    PtrRef adef;           // warped frame A' for the central warp (base null: use afl)
+    long long def_pitch;   // floats between rows of afl / bdef / adef (a multiple of 32)
+    int def_margin;        // a multiple of 4, at least R + 1
+    int *err;              // nullable: bit 0 set if a bounded wait gave up
     int w, s, R, nx, ny;
     int deform;            // 0: frame B only, 1: central
     int prec;
@@ -122,6 +124,29 @@ void prepare_pass_kernels();
 
 // Message returned by rpiv_last_error() on the calling thread.
 void set_last_error(const char *msg);
+
+// Float frames the correlation pass reads (frame A, the warped B' and A'):
+// the image sits at (M, M) of a buffer whose rows are `pitch` floats apart.
+// M is a multiple of 4 and at least R + 1, so a shifted window never leaves
+// the frame, and the pitch is a multiple of 32 floats with at least 4 floats
+// past the right margin, so that every tile row starts 16-byte aligned (for
+// a window step that is a multiple of 4) and may be copied rounded up to 16
+// bytes.
+inline int frame_margin(int max_radius) { return (max_radius + 1 + 3) / 4 * 4; }
+inline long long frame_pitch(int W, int M) { return ((long long)W + 2 * M + 4 + 31) / 32 * 32; }
+inline size_t frame_bytes(int W, int H, int M)
+{
+    return ((size_t)frame_pitch(W, M) * (size_t)(H + 2 * M) * 4 + 255) / 256 * 256;
+}
+
+// One full-resolution correlation pass on caller scratch of at least
+// single_pass_scratch_bytes(W, H, R) bytes: checks its arguments (returns a
+// public rpiv_status value, with the message set), then ingests frame A (or
+// warps A' for the central mode), warps B' and runs the pass on `st`.
+size_t single_pass_scratch_bytes(int W, int H, int R);
+int single_pass(const void *img_a, const void *img_b, size_t pitch_bytes, int fmt, int W, int H, int w, int s, int R,
+                int precision, int deform_mode, const float *pred_u, const float *pred_v, float *u, float *v,
+                int32_t *info, void *scratch, cudaStream_t st);
 
 // Returns false if (w, s, R, prec) is not supported by a compiled kernel.
 bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan);
@@ -157,11 +182,26 @@ cudaError_t launch_vort(const VortArgs &a, int n_pairs, cudaStream_t st);
 struct DownArgs {
     PtrRef src;
     int fmt;
-    long long pitch;   // bytes
-    int W, H;          // source size
-    PtrRef dst;        // float, floor(W/2) x floor(H/2), dense
+    long long pitch;     // bytes
+    int W, H;            // source size
+    PtrRef dst;          // float, floor(W/2) x floor(H/2) at (margin, margin) of rows dst_pitch floats apart
+    long long dst_pitch; // floats
+    int dst_margin;
 };
 cudaError_t launch_down(const DownArgs &a, int n_pairs, cudaStream_t st);
+
+// Frame as float into the margin layout (interior only): the correlation
+// pass reads frame A from it.
+struct IngestArgs {
+    PtrRef src;
+    int fmt;
+    long long pitch;     // bytes
+    int W, H;
+    PtrRef dst;
+    long long dst_pitch; // floats
+    int dst_margin;
+};
+cudaError_t launch_ingest(const IngestArgs &a, int n_pairs, cudaStream_t st);
 
 
 // ---------------------------------------------------------------- adjoint --

@@ -85,7 +85,7 @@ def test_noalloc_matches_scratch_entry_on_two_calls_in_a_row(lib, precision):
 
 
 def test_noalloc_rejects_images_beyond_the_static_scratch(lib):
-    # 4096 x 4096 float frame grown by 2 px needs ~67 MB > 32 MiB: rejected before any device work
+    # two 4096 x 4096 float frames need ~135 MB > 32 MiB: rejected before any device work
     big = torch.zeros((8, 8), dtype=torch.uint8, device="cuda")
     out = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
     info = torch.zeros((8, 8), dtype=torch.int32, device="cuda")
