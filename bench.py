@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--batch", type=int, default=BATCH)
     p.add_argument("--precisions", default="fp32,bf16,fp16")
-    p.add_argument("--headline", default="bf16")
+    p.add_argument("--headline", default="fp32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--latency-requests", type=int, default=200)
     p.add_argument("--mode", default="full", choices=["full", "ncu", "serve"],

@@ -13,7 +13,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/rpiv.h"
+#include "rpiv.h"
 #include "rpiv_internal.h"
 
 using namespace rpiv;

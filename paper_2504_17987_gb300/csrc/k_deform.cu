@@ -20,8 +20,9 @@ namespace rpiv {
 
 namespace {
 
-constexpr int DTX = 64, DTY = 16;  // output pixels per CTA
-constexpr int NODE_CAP = 256;      // nodes a tile can touch (checked on the host)
+constexpr int DTX = 64, DTY = 32;  // output pixels per CTA
+constexpr int DROWS = DTY / 4;     // rows per thread (256 threads = 64 columns x 4 row phases)
+constexpr int NODE_CAP = 512;      // nodes a tile can touch (checked on the host)
 
 __device__ __forceinline__ void axis_weight(int pos, int n, float c0, int s, int &i0, float &t)
 {
@@ -88,10 +89,15 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
     }
     __syncthreads();
     const int di = a.nx > 1 ? 1 : 0, dj = a.ny > 1 ? 1 : 0;
-    const int lx = threadIdx.x % DTX;
-    for (int ly = threadIdx.x / DTX; ly < DTY; ly += blockDim.x / DTX) {
-        const int x = x0 + lx, y = y0 + ly;
-        if (x >= a.W + a.M || y >= a.H + a.M) continue;
+    const int lx = threadIdx.x % DTX, ly0 = threadIdx.x / DTX;
+    const int x = x0 + lx;
+    // all rows of a thread are unrolled so that their 4 DROWS gathers are in
+    // flight together; rows and columns past the grown image are computed on
+    // clamped coordinates and not stored
+    float res[DROWS];
+#pragma unroll
+    for (int k = 0; k < DROWS; ++k) {
+        const int ly = ly0 + 4 * k, y = y0 + ly;
         float du = 0.f, dv = 0.f;
         if (has) {
             const int i0 = cix[lx], j0 = riy[ly];
@@ -115,7 +121,14 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
         const float b00 = tap<T>(img, a.pitch, xa, ya), b10 = tap<T>(img, a.pitch, xb, ya);
         const float b01 = tap<T>(img, a.pitch, xa, yb), b11 = tap<T>(img, a.pitch, xb, yb);
         const float top = b00 + tx * (b10 - b00), bot = b01 + tx * (b11 - b01);
-        out[(long long)(y + a.M) * a.out_pitch + (x + a.M)] = top + ty * (bot - top);
+        res[k] = top + ty * (bot - top);
+    }
+    if (x < a.W + a.M) {
+#pragma unroll
+        for (int k = 0; k < DROWS; ++k) {
+            const int y = y0 + ly0 + 4 * k;
+            if (y < a.H + a.M) out[(long long)(y + a.M) * a.out_pitch + (x + a.M)] = res[k];
+        }
     }
 }
 

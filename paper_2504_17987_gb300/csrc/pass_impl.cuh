@@ -153,20 +153,22 @@ static __device__ bool load_regions(const PassArgs &a, const TileGeom &g, int pa
         const float *b0 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 + M - P.padl);
         const int acols = up4(g.aw), bcols = up4(g.OFFB + g.BC);
         const uint32_t bytes = (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
-        if (tid == 0) {
+        // warp 0 alone issues the copies and polls the barrier; the other
+        // warps wait at the caller's CTA barrier, which also makes the staged
+        // rows visible to them, and leave the issue slots to co-resident CTAs
+        if (tid >= 32) return true;
+        if (lane == 0) {
             mbar_init(bar, 1);
             fence_proxy_async();
         }
-        __syncthreads();
-        if (tid < 32) {
-            if (lane == 0) mbar_expect_tx(bar, bytes);
-            __syncwarp();
-            for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
-            for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_expect_tx(bar, bytes);
+        __syncwarp();
+        for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
+        for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
         for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
             if (mbar_try_wait(bar, 0)) return true;
-        if (a.err) atomicOr(a.err, 1);
+        if (lane == 0 && a.err) atomicOr(a.err, 1);
         // give copies still in flight a bounded chance to land before the CTA exits
         for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
             if (mbar_try_wait(bar, 0)) break;
