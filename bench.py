@@ -46,13 +46,42 @@ def parse():
     p.add_argument("--headline", default="fp32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--latency-requests", type=int, default=200)
-    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve"],
+    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve", "precision"],
                    help="ncu: one warm-up step and one step of the headline path, nothing else (profiler runs); "
-                        "serve: the streaming mix (Poisson arrivals over camera streams)")
+                        "serve: the streaming mix (Poisson arrivals over camera streams); "
+                        "precision: the 8 MP Fourier-mode pair, FP32/BF16/FP16 fields against the FP64 oracle")
     p.add_argument("--requests", type=int, default=10000)
     p.add_argument("--streams", type=int, default=32)
     p.add_argument("--load", type=float, default=0.7, help="Poisson rate as a fraction of the saturation rate")
     return p.parse_args()
+
+
+# ------------------------------------------------------- replica timing --
+
+def replica_seeds(rank: int, n: int):
+    """Seeds of the distinct pairs a replica renders: disjoint across ranks."""
+    return [1002 + 100 * rank + k for k in range(n)]
+
+
+def timed_replicas(step, steps: int, warmup: int, barrier, start_timer, reduce_max) -> float:
+    """Warm-up steps, then `steps` timed steps bracketed by a barrier on both
+    sides; returns the slowest rank's elapsed milliseconds.  start_timer()
+    returns a function giving the elapsed milliseconds since it was called
+    (CUDA events on the launching stream on the GPU)."""
+    for _ in range(warmup):
+        step()
+    barrier()
+    stop = start_timer()
+    for _ in range(steps):
+        step()
+    ms = stop()
+    barrier()
+    return reduce_max(ms)
+
+
+def aggregate_rate(world: int, units_per_rank_step: int, steps: int, max_ms: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time (weak scaling)."""
+    return world * units_per_rank_step * steps / (max_ms / 1000.0)
 
 
 # ------------------------------------------------------------ CPU oracle --
@@ -188,6 +217,73 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------- precision case --
+
+def _oracle_8mp(seed: int):
+    import oracle
+    from synth import workloads as wl
+    w = wl.fourier_8mp(seed=seed)
+    A, B = w.render()
+    sc = w.schedule
+    t0 = time.perf_counter()
+    r = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels)
+    return time.perf_counter() - t0, r.u, r.v, r.vort, r.mask
+
+
+def run_precision(args):
+    """8 MP pair (3840x2160 u8, 8 Fourier modes, 48 -> 24 px, +-6, 2-level
+    pyramid): per-field error of each precision against the FP64 oracle, and
+    each precision's throughput at batch 8."""
+    import numpy as np
+    pool = mp.get_context("spawn").Pool(1)
+    pending = pool.apply_async(_oracle_8mp, (1004,))
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_17987_gb300 as rp
+    from synth import workloads as wl
+    wk = wl.fourier_8mp(seed=1004)
+    A, B = wk.render()
+    H, W = A.shape
+    a, b = rp.to_device(A), rp.to_device(B)
+    out = {}
+    fields = {}
+    for prec in ("fp32", "bf16", "fp16"):
+        cfg = rp.Config.from_schedule(W, H, wk.schedule, bit_depth=8, precision=prec, max_batch=8)
+        eng = rp.Engine(cfg)
+        res = eng.process_pair(a, b)
+        torch.cuda.synchronize()
+        fields[prec] = [t.cpu().numpy().astype(np.float64) for t in res]
+        outs = eng.empty_outputs(8)
+        for _ in range(3):
+            eng.process_batch([a] * 8, [b] * 8, outs=outs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            eng.process_batch([a] * 8, [b] * 8, outs=outs)
+        e1.record()
+        torch.cuda.synchronize()
+        out[prec] = {"pairs_per_s": 40 / (e0.elapsed_time(e1) / 1000.0)}
+        eng.close()
+    dt, ou, ov, oom, omask = pending.get()
+    pool.close()
+
+    def stats(d):
+        d = np.abs(d)
+        return {"p50": float(np.median(d)), "p99": float(np.percentile(d, 99)), "max": float(d.max()),
+                "rms": float(np.sqrt(np.mean(d * d)))}
+    for prec, (u, v, om, m) in fields.items():
+        out[prec]["err_vs_oracle"] = {"u_px": stats(u - ou), "v_px": stats(v - ov), "vort_per_frame": stats(om - oom),
+                                      "mask_agreement": float(np.mean(m == omask))}
+    line = {"mode": "precision", "workload": "fourier_8mp_u8: 3840x2160 u8, 0.05 ppp, d_p 2.5, 8 Fourier modes "
+            "(max 16 px); 2-level pyramid, 48 -> 24 px at 50 %, search +-6; 319x179 vectors",
+            "oracle_s": dt, "paths": out, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------- clocks --
 
 class ClockSampler:
@@ -254,6 +350,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "precision":
+        return run_precision(args)
     if args.mode == "serve":
         import numpy as np  # noqa: F811
         globals()["np"] = np
@@ -294,7 +392,7 @@ def main():
         return float(t.item())
 
     B = args.batch
-    seeds = [1002 + 100 * rank + k for k in range(N_DISTINCT)]
+    seeds = replica_seeds(rank, N_DISTINCT)
     pairs = [wl.paper_1mp(seed=s).render() for s in seeds]
     sched = wl.paper_1mp().schedule
     H, W = pairs[0][0].shape
@@ -326,19 +424,25 @@ def main():
         cfg = rp.Config.from_schedule(W, H, sched, bit_depth=12, precision=prec, max_batch=B)
         eng = rp.Engine(cfg, device=local)
         outs = eng.empty_outputs(B)
-        for _ in range(args.warmup):
-            eng.process_batch(a_dev, b_dev, outs=outs)
-        barrier()
         st = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as cs:
-            barrier()
+
+        def start_timer():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            for _ in range(args.steps):
-                eng.process_batch(a_dev, b_dev, outs=outs)
-            e1.record(st)
-            barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1))
+
+            def stop():
+                e1.record(st)
+                e1.synchronize()
+                return e0.elapsed_time(e1)
+            return stop
+
+        def step():
+            eng.process_batch(a_dev, b_dev, outs=outs)
+
+        for _ in range(args.warmup):
+            step()
+        with ClockSampler(local) as cs:
+            ms = timed_replicas(step, args.steps, 0, barrier, start_timer, max_over_ranks)
         if prec == args.headline:
             clocks = cs.summary()
         fields[prec] = (outs[0][0].cpu().numpy(), outs[1][0].cpu().numpy())
@@ -349,7 +453,7 @@ def main():
         recs = eng.trace_read()
         eng.trace(False)
         traces[prec] = recs
-        paths[prec] = {"pairs_per_s": world * B * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
+        paths[prec] = {"pairs_per_s": aggregate_rate(world, B, args.steps, ms), "ms_per_step": ms / args.steps,
                        "pass_ms_per_launch": {r["name"]: round(r["total_ms"] / r["launches"], 4)
                                               for r in recs if r["name"].startswith("pass/")}}
         eng.close()

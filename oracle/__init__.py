@@ -81,7 +81,7 @@ def lib():
         L.orc_gauss3.argtypes = [ctypes.c_double] * 3
         L.orc_gauss3.restype = ctypes.c_double
         L.orc_pass.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                               ctypes.c_int, _dp, _dp, _ip, _dp, _dp, _ip, _dp, _dp, _ip, _dp]
+                               ctypes.c_int, _dp, _dp, _ip, _up, _dp, _dp, _ip, _dp, _dp, _ip, _dp]
         L.orc_pass.restype = None
         L.orc_median.argtypes = [_dp, ctypes.c_int]
         L.orc_median.restype = ctypes.c_double
@@ -183,11 +183,13 @@ class PassResult:
 
 
 def correlate_pass(A, B, w: int, s: int, r: int, pu, pv, *, deform: str = "b",
-                   force_peaks=None, want_plane: bool = False) -> PassResult:
+                   force_peaks=None, want_plane: bool = False, only=None) -> PassResult:
     """One correlation pass (deform, plane, peak, Gaussian fit) on one grid.
 
     pu, pv: predictor on this grid's nodes.  deform: "b" (frame B only,
     B'(x) = B(x + d(x))) or "central" (A'(x) = A(x - d/2), B'(x) = B(x + d/2)).
+    only: optional (ny, nx) boolean mask; windows outside it are not evaluated
+    (u, v NaN, valid -1), so that large grids can be checked on a sample.
     """
     A, B, pu, pv = _f64(A), _f64(B), _f64(pu), _f64(pv)
     H, W = A.shape
@@ -210,8 +212,12 @@ def correlate_pass(A, B, w: int, s: int, r: int, pu, pv, *, deform: str = "b",
     fp = None
     if force_peaks is not None:
         fp = np.ascontiguousarray(np.asarray(force_peaks, np.int32).reshape(ny, nx, 2))
+    om = None
+    if only is not None:
+        om = np.ascontiguousarray(np.asarray(only, bool).reshape(ny, nx).astype(np.uint8))
     lib().orc_pass(_d(Aext), _d(Bext), W, H, M, w, s, r, _d(pu), _d(pv),
                    fp.ctypes.data_as(_ip) if fp is not None else None,
+                   om.ctypes.data_as(_up) if om is not None else None,
                    _d(u), _d(v), peaks.ctypes.data_as(_ip), _d(sub), _d(c5), valid.ctypes.data_as(_ip),
                    _d(plane) if plane is not None else None)
     return PassResult(u, v, peaks, sub, c5, valid, plane)

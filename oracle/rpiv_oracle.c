@@ -241,7 +241,7 @@ clamp:
  * smallest row-major index.
  */
 void orc_pass(const double *Aext, const double *Bext, int W, int H, int M, int w, int s, int r,
-              const double *pu, const double *pv, const int *force_peaks,
+              const double *pu, const double *pv, const int *force_peaks, const unsigned char *only,
               double *u, double *v, int *peaks, double *sub, double *c5, int *valid, double *plane)
 {
     const int nx = orc_grid_n(W, w, s), ny = orc_grid_n(H, w, s);
@@ -252,6 +252,12 @@ void orc_pass(const double *Aext, const double *Bext, int W, int H, int M, int w
         for (int i = 0; i < nx; ++i) {
             const int k = j * nx + i;
             const int x0 = i * s, y0 = j * s;
+            if (only && !only[k]) {
+                /* window not requested (sampled evaluation of large grids) */
+                u[k] = v[k] = NAN;
+                valid[k] = -1;
+                continue;
+            }
             for (int sy = -r; sy <= r; ++sy)
                 for (int sx = -r; sx <= r; ++sx)
                     pl[(sy + r) * np + (sx + r)] = orc_zncc(Aext, Bext, W, M, x0, y0, w, sx, sy, NULL);

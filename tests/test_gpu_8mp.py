@@ -1,0 +1,115 @@
+"""The 8 MP precision case at full size: 3840x2160 u8 pair, divergence-free
+field of 8 Fourier modes (max 16 px), passes 48 -> 24 px at 50 %, search +-6.
+
+The full-size launches are compared with the FP64 oracle on a seeded sample
+of windows (the oracle evaluates the sampled windows only), for the FP32,
+BF16 and FP16 planes; the whole pipeline is compared across precisions and
+against the analytic field, properties that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2504_17987_gb300 as rp
+import synth
+from synth import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_PX = 1e-3
+N_SAMPLE = 1500
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_2504_17987_gb300 import build
+    build.build()
+    oracle.build()
+    w = wl.fourier_8mp()
+    A, B = w.render()
+    return w, A, B
+
+
+def _sample(nx, ny, n, seed):
+    k = np.unique((synth.uniform(seed, n) * nx * ny).astype(np.int64))
+    m = np.zeros(nx * ny, bool)
+    m[k] = True
+    # the four corners and the last row/column (ragged tiles) are always checked
+    m[[0, nx - 1, nx * (ny - 1), nx * ny - 1]] = True
+    m.reshape(ny, nx)[-1, ::7] = True
+    m.reshape(ny, nx)[::7, -1] = True
+    return m.reshape(ny, nx)
+
+
+def _predictor(flow, nx, ny, w, s, seed):
+    """The analytic field at the nodes plus a smooth perturbation of +-0.4 px,
+    as a previous pass leaves it."""
+    X, Y = np.meshgrid(np.arange(nx) * s + 0.5 * (w - 1), np.arange(ny) * s + 0.5 * (w - 1))
+    tu, tv = flow.eval(X, Y)
+    r = synth.uniform(seed, 4)
+    pu = tu + 0.4 * np.sin(X / 173.0 + 6 * r[0]) * np.cos(Y / 151.0 + 6 * r[1])
+    pv = tv + 0.4 * np.cos(X / 131.0 + 6 * r[2]) * np.sin(Y / 199.0 + 6 * r[3])
+    return pu.astype(np.float32), pv.astype(np.float32)
+
+
+@pytest.mark.parametrize("w,s,R,precision", [(24, 12, 6, "fp32"), (24, 12, 6, "bf16"), (24, 12, 6, "fp16"),
+                                             (48, 24, 6, "fp32"), (48, 24, 6, "bf16")])
+def test_full_size_pass_matches_oracle_on_sampled_windows(case, w, s, R, precision):
+    flow, A, B = case[0].flow, case[1], case[2]
+    H, W = A.shape
+    nx, ny = oracle.grid_n(W, w, s), oracle.grid_n(H, w, s)
+    pu, pv = _predictor(flow, nx, ny, w, s, seed=w + R)
+    u, v, info = rp.stage_correlate(rp.to_device(A), rp.to_device(B), w, s, R, torch.from_numpy(pu).cuda(),
+                                    torch.from_numpy(pv).cuda(), precision=precision)
+    torch.cuda.synchronize()
+    valid, ky, kx = [t.cpu().numpy() for t in rp.decode_info(info)]
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    m = _sample(nx, ny, N_SAMPLE, seed=8000 + w)
+    ref = oracle.correlate_pass(A, B, w, s, R, pu.astype(np.float64), pv.astype(np.float64), want_plane=True,
+                                only=m)
+    forced = oracle.correlate_pass(A, B, w, s, R, pu.astype(np.float64), pv.astype(np.float64),
+                                   force_peaks=np.stack([ky, kx], -1).astype(np.int32), only=m)
+    assert np.array_equal(valid[m].astype(int), ref.valid[m])
+    same = (ky == ref.peaks[..., 0]) & (kx == ref.peaks[..., 1])
+    P = ref.plane.reshape(ny, nx, -1)
+    q = (ky.astype(int) + R) * (2 * R + 1) + (kx.astype(int) + R)
+    gap = P.max(axis=2) - np.take_along_axis(P, q[..., None], axis=2)[..., 0]
+    disagree = m & ~same
+    if precision == "fp32":
+        assert same[m].mean() >= 0.999, f"peak agreement {same[m].mean():.5f}"
+        assert (gap[disagree] <= 2e-5).all()
+        err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
+        assert err[m & same].max() <= TOL_PX
+    else:
+        assert same[m].mean() >= 0.99, f"{precision} peak agreement {same[m].mean():.4f}"
+        assert (gap[disagree] <= 0.02).all()
+    # at the peak the GPU chose, the FP32 refit equals the FP64 refit
+    errf = np.maximum(np.abs(u - forced.u), np.abs(v - forced.v))
+    assert errf[m].max() <= TOL_PX, f"refit at the chosen peak: {errf[m].max():.3g}"
+
+
+def test_pipeline_at_8mp_across_precisions(case):
+    wk, A, B = case
+    H, W = A.shape
+    sc = wk.schedule
+    fields = {}
+    for precision in ("fp32", "bf16", "fp16"):
+        cfg = rp.Config.from_schedule(W, H, sc, bit_depth=8, precision=precision, max_batch=1)
+        eng = rp.Engine(cfg)
+        u, v, om, mask = eng.process_pair(rp.to_device(A), rp.to_device(B))
+        torch.cuda.synchronize()
+        fields[precision] = [t.cpu().numpy() for t in (u, v, om, mask)]
+        eng.close()
+    u32, v32, om32, m32 = fields["fp32"]
+    assert u32.shape == (179, 319)
+    # against the analytic field at the nodes (the method's own accuracy, any size)
+    X, Y = np.meshgrid(np.arange(319) * 12 + 11.5, np.arange(179) * 12 + 11.5)
+    tu, tv = wk.flow.eval(X, Y)
+    e = np.hypot(u32 - tu, v32 - tv)
+    assert np.median(e) <= 0.1 and np.percentile(e, 95) <= 0.5, (np.median(e), np.percentile(e, 95))
+    assert m32.mean() >= 0.98
+    # the 16-bit planes only choose the integer peak: the fields agree with FP32
+    for precision in ("bf16", "fp16"):
+        u, v, om, m = fields[precision]
+        d = np.maximum(np.abs(u - u32), np.abs(v - v32))
+        assert np.percentile(d, 99) <= 0.01, (precision, np.percentile(d, 99))

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from synth import workloads as wl
 
 
 def _rng(seed):
@@ -308,3 +309,18 @@ def test_vorticity_lamb_oseen_within_truncation_bound():
     # and the bound is not vacuous: the peak vorticity is captured to 15 %
     k = np.unravel_index(np.argmax(ref), ref.shape)
     assert abs(om[k] - ref[k]) < 0.15 * ref[k]
+
+
+def test_sampled_window_evaluation_equals_the_full_pass():
+    # the `only` mask selects windows; it changes no arithmetic
+    w = wl.plain_256(seed=77)
+    A, B = w.render()
+    nx = oracle.grid_n(256, 32, 16)
+    rng = np.random.default_rng(5)
+    pu, pv = rng.uniform(2.5, 4.0, (nx, nx)), rng.uniform(-2.0, -1.0, (nx, nx))
+    full = oracle.correlate_pass(A, B, 32, 16, 4, pu, pv, want_plane=True)
+    m = rng.random((nx, nx)) < 0.3
+    part = oracle.correlate_pass(A, B, 32, 16, 4, pu, pv, want_plane=True, only=m)
+    assert np.array_equal(part.u[m], full.u[m]) and np.array_equal(part.v[m], full.v[m])
+    assert np.array_equal(part.peaks[m], full.peaks[m]) and np.array_equal(part.plane[m], full.plane[m])
+    assert np.all(part.valid[~m] == -1) and np.all(np.isnan(part.u[~m]))
