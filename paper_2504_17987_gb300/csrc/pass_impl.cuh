@@ -85,14 +85,6 @@ struct TileGeom {
     int nbx, nby, nb;
 };
 
-// Rows of each 16-bit B' copy: the A fragments of an m-tile stack read up to
-// 16 * MT rows below the first row of the last 8-row sub-block.
-__host__ __device__ inline int tc_b_rows(int BR, int ah, int R)
-{
-    const int MT = (8 + 2 * R + 15) / 16;
-    return (BR > ah + 16 * MT ? BR : ah + 16 * MT) + 8;
-}
-
 // ------------------------------------------------------- region loads --
 
 constexpr int MBAR_SPIN_LIMIT = 1 << 22;  // bounded wait for the bulk copies
@@ -193,15 +185,13 @@ __device__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As,
     const int tid = threadIdx.x;
     for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next())
         TA[it.y * P.tca_pitch + it.x] = to_h16<PREC>(As[it.y * P.a_pitch + it.x]);
-    const int brows = tc_b_rows(g.BR, g.ah, g.R);
-    uint16_t *TB1 = TB + brows * P.tcb_pitch;
+    uint16_t *TB1 = TB + P.tb_rows * P.tcb_pitch;
     const int lo = g.OFFB, hi = g.OFFB + g.BC;  // staged columns
-    const int cols = hi + 8;                     // fragments reach at most 8 columns past the region
-    for (Walk2D it(tid, blockDim.x, cols); it.y < brows; it.next()) {
+    const int cols = P.tb_cols;                  // fragments of unused shifts reach past the region: zeros
+    for (Walk2D it(tid, blockDim.x, cols); it.y < g.BR; it.next()) {
         const int y = it.y, x = it.x;
-        const bool row_ok = y < g.BR;
-        const float v0 = (row_ok && x >= lo && x < hi) ? Bs[y * P.b_pitch + x] : 0.f;
-        const float v1 = (row_ok && x + 1 >= lo && x + 1 < hi) ? Bs[y * P.b_pitch + x + 1] : 0.f;
+        const float v0 = (x >= lo && x < hi) ? Bs[y * P.b_pitch + x] : 0.f;
+        const float v1 = (x + 1 >= lo && x + 1 < hi) ? Bs[y * P.b_pitch + x + 1] : 0.f;
         TB[y * P.tcb_pitch + x] = to_h16<PREC>(v0);
         TB1[y * P.tcb_pitch + x] = to_h16<PREC>(v1);
     }
@@ -425,95 +415,125 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
     }
 }
 
-// One warp per (block, 8-row sub-block).  For each chunk of at most 9 shifts
-// sx the accumulators D[i][j] (i: B' row offset, j: A row offset) are summed
-// over the sub-block's 8-column chunks; shift sy = i - j - R is recovered from
-// the diagonals through a per-warp scratch buffer.
-template <int R, int PREC>
-__device__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint16_t *TA, const uint16_t *TB,
-                                float *scratch, float *Ps)
+template <int PREC>
+__device__ __forceinline__ void mma_k16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                        uint32_t b0, uint32_t b1)
 {
-    constexpr int ND = 2 * R + 1;
-    constexpr int NP = ND * ND;
-    constexpr int MT = (8 + 2 * R + 15) / 16;
-    constexpr int SXC = ND < 3 ? ND : 3;
-    const PassPlan &P = a.plan;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int gq = lane >> 2, tq = lane & 3;
-    const int G = P.G;
-    const int nsb = (G + 7) / 8, nkc = (G + 7) / 8;
-    const int brows = tc_b_rows(g.BR, g.ah, R);
-    const uint16_t *TB1 = TB + brows * P.tcb_pitch;
-    float *scr = scratch + warp * (SXC * 16 * MT * 9);
-    const int items = g.nb * nsb;
-    for (int it = warp; it < items; it += nwarps) {
-        const int b = it / nsb, sb = it - b * nsb;
-        const int bxi = b % g.nbx, byi = b / g.nbx;
-        const int Y0 = byi * G + sb * 8;  // first A row of the sub-block (A-region coords)
-        const int X0 = bxi * G;
-        const bool row_ok = (sb * 8 + gq) < G;
-        for (int sx0 = -R; sx0 <= R; sx0 += SXC) {
-            float acc[SXC][MT][4];
-#pragma unroll
-            for (int q = 0; q < SXC; ++q)
-#pragma unroll
-                for (int m = 0; m < MT; ++m)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[q][m][e] = 0.f;
-            for (int kc = 0; kc < nkc; ++kc) {
-                const int X = X0 + kc * 8;
-                const bool col_ok = (kc * 8 + 2 * tq) < G;
-                const uint32_t bfrag =
-                    (row_ok && col_ok)
-                        ? *reinterpret_cast<const uint32_t *>(TA + (Y0 + gq) * P.tca_pitch + X + 2 * tq)
-                        : 0u;
-#pragma unroll
-                for (int q = 0; q < SXC; ++q) {
-                    const int sx = sx0 + q;
-                    if (sx > R) break;
-                    // smem column of A column X + 2tq at shift sx; pick the copy that makes it even
-                    const int col = X + 2 * tq + sx + P.padl;
-                    const uint16_t *src = (col & 1) ? TB1 : TB;
-                    const int c2 = col & ~1;
-#pragma unroll
-                    for (int m = 0; m < MT; ++m) {
-                        // B' logical row of A row Y0 + i - R is Y0 + i + 1
-                        const int r0 = Y0 + 1 + 16 * m + gq;
-                        const uint32_t a0 = *reinterpret_cast<const uint32_t *>(src + r0 * P.tcb_pitch + c2);
-                        const uint32_t a1 = *reinterpret_cast<const uint32_t *>(src + (r0 + 8) * P.tcb_pitch + c2);
-                        mma_k8<PREC>(acc[q][m], a0, a1, bfrag);
-                    }
-                }
-            }
-            // store the accumulator tiles (row pitch 9: conflict-free diagonal reads)
-#pragma unroll
-            for (int q = 0; q < SXC; ++q) {
-#pragma unroll
-                for (int m = 0; m < MT; ++m) {
-                    float *t = scr + (q * 16 * MT + 16 * m) * 9;
-                    t[gq * 9 + 2 * tq] = acc[q][m][0];
-                    t[gq * 9 + 2 * tq + 1] = acc[q][m][1];
-                    t[(gq + 8) * 9 + 2 * tq] = acc[q][m][2];
-                    t[(gq + 8) * 9 + 2 * tq + 1] = acc[q][m][3];
-                }
-            }
-            __syncwarp();
-            // shift sy = d - R is the diagonal i - j = d of the tile
-            const int nq = min(SXC, R - sx0 + 1);
-            for (int o = lane; o < nq * ND; o += 32) {
-                const int q = o / ND, d = o - q * ND;
-                const float *t = scr + q * 16 * MT * 9 + d * 9;
-                float sum = 0.f;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) sum += t[j * 10];
-                Ps[(size_t)(b * nsb + sb) * NP + d * ND + (sx0 + q + R)] = sum;
-            }
-            __syncwarp();
-        }
+    if (PREC == PREC_BF16) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    } else {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
     }
 }
 
+__device__ __forceinline__ uint32_t ld_pair(const uint16_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+// Block planes on the tensor cores, one warp per (block, row group).  For
+// every row r of B' the block meets, the MMA multiplies
+//     X_r[sx][k] = B'[r][x0 + k + sx]        (a Toeplitz matrix of the row: M = sx)
+// by  Y_r[k][sy] = A[r - sy][x0 + k]        (the A rows r - sy of the group: N = sy)
+// over the block's columns k, so D[sx][sy] accumulates
+//     sum_r sum_k A[r - sy][x0 + k] B'[r][x0 + k + sx] = P_b(sy, sx)
+// directly, for every shift, across the rows (A rows outside the group enter
+// as zeros).  16 x 8 tiles: MT tiles of sx, NT tiles of sy.
+template <int R, int PREC>
+__device__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint16_t *TA, const uint16_t *TB,
+                                float *Ps)
+{
+    constexpr int ND = 2 * R + 1;
+    constexpr int NP = ND * ND;
+    constexpr int MT = (ND + 15) / 16;
+    constexpr int NT = (ND + 7) / 8;
+    const PassPlan &P = a.plan;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int G = P.G, RG = P.RGx, rows = G / RG;
+    const uint16_t *TB1 = TB + P.tb_rows * P.tcb_pitch;
+    // smem column of Toeplitz element (m, k) of m-tile mt at block column X:
+    //     padl - R + X + 16 mt + m + k;  X is even, so its parity is that of padl - R + m
+    const int colbase = P.padl - R + gq + 2 * tq;
+    // odd columns read the copy shifted by one (TB1[x] = B'[x + 1]) at x - 1
+    const uint16_t *srcB = (colbase & 1) ? (TB1 - 1) : TB;
+    const bool k16 = (G % 16) == 0;
+    const int items = g.nb * RG;
+    for (int it = warp; it < items; it += nwarps) {
+        const int b = it / RG, gi = it - b * RG;
+        const int bxi = b % g.nbx, byi = b / g.nbx;
+        const int X0 = bxi * G;
+        const int i_lo = byi * G + gi * rows, i_hi = i_lo + rows;  // A rows of the group
+        float acc[MT][NT][4];
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[m][n][e] = 0.f;
+        // smem rows of B': A row i at shift sy meets smem row i + sy + R + 1
+        for (int br = i_lo + 1; br <= i_hi - 1 + 2 * R + 1; ++br) {
+            const uint16_t *brow = srcB + br * P.tcb_pitch;
+            // A row of this lane's sy column n = gq in n-tile nt: i = br - 1 - 8 nt - gq
+            const uint16_t *arow[NT];
+            bool aok[NT];
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const int i = br - 1 - 8 * n - gq;
+                aok[n] = i >= i_lo && i < i_hi;
+                arow[n] = TA + (aok[n] ? i : i_lo) * P.tca_pitch + 2 * tq;
+            }
+            if (k16) {
+                for (int X = X0; X < X0 + G; X += 16) {
+                    uint32_t bf[NT][2];
+#pragma unroll
+                    for (int n = 0; n < NT; ++n) {
+                        bf[n][0] = aok[n] ? ld_pair(arow[n] + X) : 0u;
+                        bf[n][1] = aok[n] ? ld_pair(arow[n] + X + 8) : 0u;
+                    }
+#pragma unroll
+                    for (int m = 0; m < MT; ++m) {
+                        const uint16_t *c = brow + colbase + X + 16 * m;
+                        const uint32_t a0 = ld_pair(c), a1 = ld_pair(c + 8), a3 = ld_pair(c + 16);
+#pragma unroll
+                        for (int n = 0; n < NT; ++n) mma_k16<PREC>(acc[m][n], a0, a1, a1, a3, bf[n][0], bf[n][1]);
+                    }
+                }
+            } else {
+                for (int X = X0; X < X0 + G; X += 8) {
+                    const bool cok = (X - X0) + 2 * tq < G;  // columns past an uneven block enter as zeros
+                    uint32_t bf[NT];
+#pragma unroll
+                    for (int n = 0; n < NT; ++n) bf[n] = (aok[n] && cok) ? ld_pair(arow[n] + X) : 0u;
+#pragma unroll
+                    for (int m = 0; m < MT; ++m) {
+                        const uint16_t *c = brow + colbase + X + 16 * m;
+                        const uint32_t a0 = ld_pair(c), a1 = ld_pair(c + 8);
+#pragma unroll
+                        for (int n = 0; n < NT; ++n) mma_k8<PREC>(acc[m][n], a0, a1, bf[n]);
+                    }
+                }
+            }
+        }
+        // D[m][n] of tile (mt, nt) is P_b(sy = 8 nt + n - R, sx = 16 mt + m - R)
+        float *out = Ps + (size_t)(b * RG + gi) * NP;
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int sx = 16 * m + gq + (e >= 2 ? 8 : 0) - R;
+                    const int sy = 8 * n + 2 * tq + (e & 1) - R;
+                    if (sx <= R && sy <= R) out[(sy + R) * ND + (sx + R)] = acc[m][n][e];
+                }
+    }
+}
 
 // ----------------------------------------------- assembly and sub-pixel --
 
@@ -793,20 +813,24 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
     ws.need = reinterpret_cast<int *>(smem + P.off_need);
     ws.dpart = reinterpret_cast<float *>(smem + P.off_dpart);
 
-    // 1: A and B' regions (and their 16-bit copies on the tensor-core path)
+    // 1: A and B' regions
     // every thread leaves together if any thread's bounded wait gave up (error word set)
     const bool loaded = load_regions(a, g, pair, As, Bs, bar);
     if (__syncthreads_or(!loaded)) {
         invalid_tile(a, g, pair);
         return;
     }
-    if (PREC != PREC_FP32) tc_copies<PREC>(a, g, As, Bs, TA, TB);
 
     // 2: A window statistics, box sums of B' for every window and shift
     block_stats(a, g, As, bst);
     box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
     __syncthreads();
     window_stats(a, g, bst, stats);
+    if (PREC != PREC_FP32) {
+        // 16-bit copies of the regions for the tensor cores, over the dead C region
+        tc_copies<PREC>(a, g, As, Bs, TA, TB);
+        __syncthreads();
+    }
 
     // 3: block partial planes (alias the dead C region)
     if (PREC == PREC_FP32) {
@@ -815,8 +839,7 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
         else
             block_planes_fp32_generic(a, g, As, Bs, Ps);
     } else {
-        float *scr = reinterpret_cast<float *>(smem + P.off_scr);
-        block_planes_tc<(RC >= 0 ? RC : 0), PREC>(a, g, TA, TB, scr, Ps);
+        block_planes_tc<(RC >= 0 ? RC : 0), PREC>(a, g, TA, TB, Ps);
     }
     __syncthreads();
 

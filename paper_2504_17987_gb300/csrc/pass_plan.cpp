@@ -99,7 +99,15 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
         }
         p.RGx = RG;
     } else {
-        p.RGx = (G + 7) / 8;
+        // warp per (block, row group): enough groups for the CTA's warps
+        int RG = 1;
+        while (nb * RG < kThreads / 32) {
+            int nx = RG + 1;
+            while (nx < G && G % nx) ++nx;
+            if (nx > G || G / nx < 2) break;
+            RG = nx;
+        }
+        p.RGx = RG;
     }
     int off = 0;
     auto take = [&](int bytes) {
@@ -113,32 +121,44 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     p.off_stats = take(2 * nwin * 4);
     p.off_red = take(16);      // the region loads' mbarrier
     p.off_gst = take(nb * 8);  // per-block (sum, centred sum of squares) of A
-    if (prec != PREC_FP32) {
-        const int MT = (8 + 2 * R + 15) / 16;
-        const int OFFB = p.padl - (R + 1);
-        p.tca_pitch = odd8(aw + 8);
-        p.tcb_pitch = odd8(OFFB + BC + 9);
-        const int ta_rows = up(ah, 8) + 8;
-        const int tb_rows = std::max(BR, ah + 16 * MT) + 8;
-        p.off_tca = take(ta_rows * p.tca_pitch * 2);
-        p.off_tcb = take(2 * tb_rows * p.tcb_pitch * 2);
-    }
-    // region reused over the phases: C (box sums) -> P (block planes) + TC
-    // epilogue scratch -> P + per-window stencil buffers
+    // region reused over the phases:
+    //   FP32: C (column box sums) -> P (block planes) + per-window stencil buffers
+    //   TC:   C -> 16-bit copies TA, TB + P -> per-window buffers (over TA, TB) + P
     const int c_bytes = 2 * vh * p.h_pitch * 4;
     const int p_bytes = up(nb * p.RGx * NP * 4, 16);
-    const int sxc = ND < 3 ? ND : 3;
-    const int MT = (8 + 2 * R + 15) / 16;
-    const int scr_bytes = prec != PREC_FP32 ? up((kThreads / 32) * sxc * 16 * MT * 9 * 4, 16) : 0;
     const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(nwin * ngr * 5 * 4, 16);
     p.off_h = off;
-    p.off_p = off;
-    p.off_scr = off + p_bytes;
-    p.off_c5 = off + p_bytes;
+    int region = 0, win_off = 0;
+    if (prec == PREC_FP32) {
+        p.off_p = off;
+        win_off = off + p_bytes;
+        region = std::max(c_bytes, p_bytes + win_bytes);
+    } else {
+        // Toeplitz fragments of unused shifts reach 16 MT (+ 8 for uneven
+        // blocks) columns past the last window column: those columns hold zeros
+        const int MT = (ND + 15) / 16;
+        p.tb_rows = BR;
+        p.tb_cols = up(p.padl - R + aw + 16 * MT + 8, 2);
+        p.tca_pitch = odd8(aw);
+        p.tcb_pitch = odd8(p.tb_cols);
+        const int ta_bytes = up(ah * p.tca_pitch * 2, 16);
+        const int tb_bytes = up(2 * p.tb_rows * p.tcb_pitch * 2, 16);
+        p.off_tca = off;
+        p.off_tcb = off + ta_bytes;
+        p.off_p = off + ta_bytes + tb_bytes;
+        if (win_bytes <= ta_bytes + tb_bytes) {
+            win_off = off;
+            region = std::max(c_bytes, ta_bytes + tb_bytes + p_bytes);
+        } else {
+            win_off = p.off_p + p_bytes;
+            region = std::max(c_bytes, ta_bytes + tb_bytes + p_bytes + win_bytes);
+        }
+    }
+    p.off_c5 = win_off;
     p.off_peaks = p.off_c5 + up(nwin * 5 * 4, 16);
     p.off_need = p.off_peaks + up(nwin * 4, 16);
     p.off_dpart = p.off_need + up(nwin * 4, 16);
-    off = up(off + std::max(c_bytes, p_bytes + std::max(scr_bytes, win_bytes)), 16);
+    off = up(off + region, 16);
     p.smem_bytes = off;
     p.max_windows = nwin;
     p.max_blocks = nb;

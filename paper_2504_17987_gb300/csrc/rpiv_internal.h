@@ -75,8 +75,8 @@ struct PassPlan {
     int off_v;                   // V1 then V2 (window box sums), same pitch
     int off_p;                   // block partial planes (aliases H)
     int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
-    int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path), elements
-    int off_scr;                 // TC epilogue scratch
+    int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path; aliases H), elements
+    int tb_rows, tb_cols;        // rows of each B' copy, columns written
     int off_stats;               // per-window mean / energy of A
     int off_red;                 // mbarrier of the bulk region loads
     int off_gst;                 // per-G x G block sum and centred sum of squares of A
