@@ -30,6 +30,8 @@ if ROOT not in sys.path:
 METRIC = "1 MP PIV pairs/s and p99 latency, BF16 vs FP32 path at ≤0.01 px error vs oracle"
 N_DISTINCT = 8          # distinct synthetic pairs, replicated to fill a batch
 BATCH = 64
+WORKLOAD_R1 = ("paper_1mp_16px_r1: the 1 MP pair below with the paper's own operating point: 2-level pyramid, "
+               "32 px (+-4) -> 16 px at 50% with a +-1 stencil search; 127x127 vectors")
 WORKLOAD = ("paper_1mp_u16: 1024x1024 uint16 (12-bit) pair, 0.03 ppp, d_p U(2,4), 10% particle loss, "
             "uniform 12 px + tanh shear + Lamb-Oseen; 2-level pyramid, passes 64->32->16 px, 50% overlap, "
             "search +-4; 127x127 vectors")
@@ -46,7 +48,9 @@ def parse():
     p.add_argument("--headline", default="fp32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--latency-requests", type=int, default=200)
-    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve", "precision"],
+    p.add_argument("--workload", default="paper_1mp", choices=["paper_1mp", "paper_1mp_r1"],
+                   help="paper_1mp_r1: the paper's 16 px / +-1 operating point on the same images")
+    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve", "precision", "adjoint"],
                    help="ncu: one warm-up step and one step of the headline path, nothing else (profiler runs); "
                         "serve: the streaming mix (Poisson arrivals over camera streams); "
                         "precision: the 8 MP Fourier-mode pair, FP32/BF16/FP16 fields against the FP64 oracle")
@@ -86,14 +90,16 @@ def aggregate_rate(world: int, units_per_rank_step: int, steps: int, max_ms: flo
 
 # ------------------------------------------------------------ CPU oracle --
 
-def _oracle_pair(seed: int):
-    """Render one pair and run the FP64 oracle on it; returns timing and field."""
+def _oracle_pair(job):
+    """Render one pair and run the FP64 oracle on it; returns timing and field.
+    job: a seed, or (seed, workload name)."""
     import numpy as np  # noqa: F401
     import oracle
     from synth import workloads as wl
+    seed, name = (job, "paper_1mp") if isinstance(job, int) else job
     w = wl.paper_1mp(seed=seed)
     A, B = w.render()
-    sc = w.schedule
+    sc = (wl.paper_1mp_r1(seed=seed) if name == "paper_1mp_r1" else w).schedule
     t0 = time.perf_counter()
     r = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels)
     dt = time.perf_counter() - t0
@@ -284,6 +290,55 @@ def run_precision(args):
     return 0
 
 
+# ------------------------------------------------------ differentiation --
+
+def run_adjoint(args):
+    """Score and gradient through the warp at 1 MP (u8, 32 px at 75 %, 125x125
+    nodes): time of rpiv_backward, and the 5-step gradient refinement."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_17987_gb300 as rp
+    import synth
+    from synth import workloads as wl
+    wk = wl.diff_1mp()
+    A, B = wk.render()
+    H, W = A.shape
+    cfg = rp.Config(W, H, windows=(32,), overlaps=(0.75,), radii=(8,), bit_depth=8)
+    eng = rp.Engine(cfg)
+    a, b = rp.to_device(A), rp.to_device(B)
+    X, Y = np.meshgrid(np.arange(125) * 8 + 15.5, np.arange(125) * 8 + 15.5)
+    tu, tv = wk.flow.eval(X, Y)
+    r = synth.uniform(3003, 2 * 125 * 125).reshape(2, 125, 125)
+    u = torch.from_numpy((tu + 0.3 * (r[0] - 0.5)).astype(np.float32)).cuda()
+    v = torch.from_numpy((tv + 0.3 * (r[1] - 0.5)).astype(np.float32)).cuda()
+    for _ in range(3):
+        eng.score_and_grad(a, b, u, v)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        eng.score_and_grad(a, b, u, v)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    rp.refine(eng, a, b, u, v, steps=5)  # first use: lazy module and allocator warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, hist = rp.refine(eng, a, b, u, v, steps=5)
+    torch.cuda.synchronize()
+    ref_ms = 1000 * (time.perf_counter() - t0)
+    e_before = float(np.median(np.hypot(u.cpu().numpy() - tu, v.cpu().numpy() - tv)))
+    line = {"mode": "adjoint", "workload": "diff_1mp_u8: 1024x1024 u8, 32 px at 75 %, 125x125 nodes",
+            "score_and_grad_ms": ms, "refine_5_steps_ms": ref_ms, "score_history": hist,
+            "median_error_px_before": e_before, "data": "synthetic"}
+    eng.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------- clocks --
 
 class ClockSampler:
@@ -352,6 +407,8 @@ def main():
         return run_reference(args)
     if args.mode == "precision":
         return run_precision(args)
+    if args.mode == "adjoint":
+        return run_adjoint(args)
     if args.mode == "serve":
         import numpy as np  # noqa: F811
         globals()["np"] = np
@@ -394,7 +451,8 @@ def main():
     B = args.batch
     seeds = replica_seeds(rank, N_DISTINCT)
     pairs = [wl.paper_1mp(seed=s).render() for s in seeds]
-    sched = wl.paper_1mp().schedule
+    sched = (wl.paper_1mp_r1() if args.workload == "paper_1mp_r1" else wl.paper_1mp()).schedule
+    workload = WORKLOAD_R1 if args.workload == "paper_1mp_r1" else WORKLOAD
     H, W = pairs[0][0].shape
     a_dev = [rp.to_device(pairs[i % N_DISTINCT][0], dev) for i in range(B)]
     b_dev = [rp.to_device(pairs[i % N_DISTINCT][1], dev) for i in range(B)]
@@ -565,7 +623,7 @@ def main():
     accuracy = {}
     if pool is not None:
         sample_seeds = [1002 + k for k in range(cores)]
-        dt, res = oracle_round(pool, sample_seeds)
+        dt, res = oracle_round(pool, [(sd, args.workload) for sd in sample_seeds])
         pool.close()
         cpu = {"value": len(sample_seeds) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(sample_seeds)} pairs of the workload, one per core, FP64 oracle, "
@@ -586,7 +644,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": paths[head]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "batch_pairs_per_gpu": B, "precision": head,
+            "config": {"workload": workload, "batch_pairs_per_gpu": B, "precision": head,
                        "l2": f"inputs {in_bytes / 2**20:.0f} MiB per step > 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "paths": paths, "latency": latency, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,

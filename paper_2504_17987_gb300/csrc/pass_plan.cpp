@@ -32,11 +32,13 @@ void prepare_pass_kernels()
 namespace {
 
 constexpr int kThreads = 256;
-// Shared memory a tile may use (228 KB per SM, 1 KB reserved per CTA).  The
-// FP32 kernel runs best at about four CTAs per SM (56 KB), the tensor-core
-// kernel, whose 16-bit copies double the staged bytes, at two (112 KB); both
-// measured on GB300 over 40..112 KB.  RPIV_TILE_SMEM_KB overrides it (tuning).
-int smem_budget(int prec)
+// Shared memory a tile may use (228 KB per SM, 1 KB reserved per CTA),
+// chosen from sweeps of 40..220 KB on GB300 at 16 MP per pass: the FP32
+// kernel runs best at four CTAs per SM (56 KB) up to r = 4 and at three
+// (72 KB) for larger radii, whose per-tile halo grows; the tensor-core kernel
+// at 72 KB for 8-px blocks and 112 KB for larger blocks, whose windows then
+// share more blocks.  RPIV_TILE_SMEM_KB overrides it (tuning).
+int smem_budget(int prec, int R, int G)
 {
     static int kb = [] {
         const char *e = std::getenv("RPIV_TILE_SMEM_KB");
@@ -44,7 +46,8 @@ int smem_budget(int prec)
         return (v >= 16 && v <= 227) ? v : 0;
     }();
     if (kb) return kb * 1024;
-    return (prec == PREC_FP32 ? 56 : 112) * 1024;
+    if (prec == PREC_FP32) return (R >= 6 ? 72 : 56) * 1024;
+    return (G >= 16 ? 112 : 72) * 1024;
 }
 constexpr int kSmemMax = 227 * 1024;
 
@@ -187,7 +190,7 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan)
     for (int t = 8; t >= 1; --t) {
         const int TX = std::min(t, nx), TY = std::min(t, ny);
         Layout L = layout_for(TX, TY, w, s, R, G, prec);
-        if (L.bytes <= smem_budget(prec) || (t == 1 && L.bytes <= kSmemMax)) {
+        if (L.bytes <= smem_budget(prec, R, G) || (t == 1 && L.bytes <= kSmemMax)) {
             *plan = L.p;
             plan->tiles_x = (nx + TX - 1) / TX;
             plan->tiles_y = (ny + TY - 1) / TY;

@@ -289,18 +289,23 @@ class GpuExecutor(Executor):
     CUDA stream per slot, so batches in different slots overlap."""
 
     def __init__(self, slots: int, precision: str = "bf16", max_batch: int = 64, cold_batch: int = 8,
-                 device: int = 0):
+                 device: int = 0, max_megapixels: float = 16.0):
         import torch
         self.torch = torch
         self.precision = precision
         self.max_batch = max_batch
         self.cold_batch = cold_batch
+        # pixels per launch are capped so that a batch of large frames holds
+        # the GPU for about as long as a batch of small ones (tail latency)
+        self.max_megapixels = max_megapixels
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.engines = {}
 
     def max_pairs(self, key: Key, mode: str) -> int:
-        return self.cold_batch if mode == COLD else self.max_batch
+        cap = self.cold_batch if mode == COLD else self.max_batch
+        mp = key[0] * key[1] / 1e6
+        return max(1, min(cap, int(self.max_megapixels // mp)))
 
     def _cfg(self, key: Key, mode: str):
         W, H, bits = key
