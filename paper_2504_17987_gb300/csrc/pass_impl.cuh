@@ -232,7 +232,8 @@ static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const floa
         }
     }
     __syncthreads();
-    float *V1 = Vs, *V2 = Vs + g.vh * cp;
+    const int vp = P.v_pitch;  // pitch of V (odd, >= hw)
+    float *V1 = Vs, *V2 = Vs + g.vh * vp;
     const int nsegh = (g.hw + 7) / 8;
     for (int it = tid; it < g.vh * nsegh; it += blockDim.x) {
         const int seg = it / g.vh, r = it - seg * g.vh;
@@ -243,13 +244,13 @@ static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const floa
             s1 += c1[x];
             s2 += c2[x];
         }
-        V1[r * cp + c_lo] = s1;
-        V2[r * cp + c_lo] = s2;
+        V1[r * vp + c_lo] = s1;
+        V2[r * vp + c_lo] = s2;
         for (int c = c_lo + 1; c < c_hi; ++c) {
             s1 += c1[c + w - 1] - c1[c - 1];
             s2 += c2[c + w - 1] - c2[c - 1];
-            V1[r * cp + c] = s1;
-            V2[r * cp + c] = s2;
+            V1[r * vp + c] = s1;
+            V2[r * vp + c] = s2;
         }
     }
 }
@@ -597,7 +598,7 @@ static __device__ void plane_and_peak(const PassArgs &a, const TileGeom &g, cons
     const int ND = 2 * R + 1, NP = ND * ND;
     const int G = P.G, kb = a.w / G, RG = P.RGx;
     const float inv_n = 1.f / (float)(a.w * a.w), tau = TAU_PER_PIXEL * (float)(a.w * a.w);
-    const int cp = P.h_pitch;
+    const int cp = P.v_pitch;
     const float *V1 = Vs, *V2 = Vs + g.vh * cp;
     for (int wi = warp; wi < g.nwin; wi += nwarps) {
         const int wxi = wi % g.nwx, wyi = wi / g.nwx;
@@ -706,7 +707,7 @@ static __device__ void finalize(const PassArgs &a, const TileGeom &g, const floa
     const PassPlan &P = a.plan;
     const int w = a.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
     const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
-    const int cp = P.h_pitch;
+    const int cp = P.v_pitch;
     const float *V1 = Vs, *V2 = Vs + g.vh * cp;
     const float *pu = (const float *)resolve(a.pred_u, pair);
     const float *pv = (const float *)resolve(a.pred_v, pair);

@@ -92,6 +92,7 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     p.a_pitch = odd4(aw);
     p.b_pitch = odd4(p.padl + aw + R + 4);
     p.h_pitch = BC | 1;
+    p.v_pitch = (BC - w + 1) | 1;
     if (prec == PREC_FP32) {
         // partial planes per block: enough (block, sy, row-group) items to fill the CTA
         int RG = 1;
@@ -120,7 +121,7 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     };
     p.off_a = take(ah * p.a_pitch * 4);
     p.off_b = take(BR * p.b_pitch * 4);
-    p.off_v = take(2 * vh * p.h_pitch * 4);
+    p.off_v = take(2 * vh * p.v_pitch * 4);
     p.off_stats = take(2 * nwin * 4);
     p.off_red = take(16);      // the region loads' mbarrier
     p.off_gst = take(nb * 8);  // per-block (sum, centred sum of squares) of A

@@ -72,7 +72,7 @@ struct PassPlan {
     int off_a, a_pitch;          // A region, floats
     int off_b, b_pitch, padl;    // B' region, floats; logical column 0 at padl - (R+1)
     int off_h, h_pitch;          // C1 then C2 (column box sums), floats; odd pitch >= BC
-    int off_v;                   // V1 then V2 (window box sums), same pitch
+    int off_v, v_pitch;          // V1 then V2 (window box sums), floats; odd pitch >= hw
     int off_p;                   // block partial planes (aliases H)
     int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
     int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path; aliases H), elements
