@@ -32,24 +32,41 @@ void prepare_pass_kernels()
 namespace {
 
 constexpr int kThreads = 256;
-// Shared memory a tile may use (228 KB per SM, 1 KB reserved per CTA),
-// chosen from sweeps of 40..220 KB on GB300 at 16 MP per pass: the FP32
-// kernel runs best at four CTAs per SM (56 KB) up to r = 4 and at three
-// (72 KB) for larger radii, whose per-tile halo grows; the tensor-core kernel
-// at 72 KB for 8-px blocks and 112 KB for larger blocks, whose windows then
-// share more blocks.  RPIV_TILE_SMEM_KB overrides it (tuning).
-int smem_budget(int prec, int R, int G)
+// RPIV_TILE_SMEM_KB caps the shared memory of a tile (tuning).
+int smem_budget_override()
 {
     static int kb = [] {
         const char *e = std::getenv("RPIV_TILE_SMEM_KB");
         const int v = e ? std::atoi(e) : 0;
         return (v >= 16 && v <= 227) ? v : 0;
     }();
-    if (kb) return kb * 1024;
+    return kb;
+}
+
+// Shared memory a tensor-core tile may use (228 KB per SM, 1 KB reserved per
+// CTA), from sweeps of 40..220 KB on GB300 at 16 MP per pass: 72 KB for 8-px
+// blocks, 112 KB for larger blocks, whose windows then share more blocks.
+int smem_budget(int prec, int R, int G)
+{
+    if (const int kb = smem_budget_override()) return kb * 1024;
     if (prec == PREC_FP32) return (R >= 6 ? 72 : 56) * 1024;
     return (G >= 16 ? 112 : 72) * 1024;
 }
 constexpr int kSmemMax = 227 * 1024;
+
+// (block, sy, row group) items the FP32 plane loop aims for before it stops
+// splitting blocks into row groups: half the CTA's threads (swept on GB300:
+// 64..512, 128 best; more groups cost more partial planes to sum).
+// RPIV_PLANE_ITEMS overrides it (tuning).
+int plane_items()
+{
+    static int n = [] {
+        const char *e = std::getenv("RPIV_PLANE_ITEMS");
+        const int v = e ? std::atoi(e) : 0;
+        return (v >= 1 && v <= 4096) ? v : kThreads / 2;
+    }();
+    return n;
+}
 
 int gcd(int a, int b)
 {
@@ -96,7 +113,7 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     if (prec == PREC_FP32) {
         // partial planes per block: enough (block, sy, row-group) items to fill the CTA
         int RG = 1;
-        while (RG < G && nb * ND * RG < kThreads) {
+        while (RG < G && nb * ND * RG < plane_items()) {
             int nx = RG + 1;
             while (nx < G && G % nx) ++nx;
             RG = nx;
@@ -183,11 +200,68 @@ bool pass_supported(int R, int prec)
     return false;
 }
 
+// CTAs per SM an FP32 tile must leave room for.  Swept on GB300 at 16 MP per
+// pass (targets 2..5): windows of 48 px and more run best at three CTAs, whose
+// larger tiles let neighbouring windows share their blocks (64 px: 0.78 ->
+// 0.59 ms); 24..40 px at four; smaller windows at five.  RPIV_MIN_CTAS
+// overrides it (tuning).
+int min_ctas(int w)
+{
+    static int n = [] {
+        const char *e = std::getenv("RPIV_MIN_CTAS");
+        const int v = e ? std::atoi(e) : 0;
+        return (v >= 1 && v <= 8) ? v : 0;
+    }();
+    if (n) return n;
+    return w >= 48 ? 3 : (w >= 24 ? 4 : 5);
+}
+
+// FP32 tiles: among shapes of up to 8 x 8 windows (not necessarily square)
+// that leave room for min_ctas() CTAs per SM, counting shared memory (228 KB
+// per SM, 1 KB reserved per CTA), threads and registers (48 per thread, 64
+// for r = 8), the one with the most windows; ties go to fewer blocks per
+// window, then to the squarer tile.  If none fits, the shape with the most
+// CTAs per SM.
+bool plan_fp32(int w, int s, int R, int G, int nx, int ny, PassPlan *plan)
+{
+    const int regs = R >= 8 ? 64 : 48;
+    const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
+    const int override_kb = smem_budget_override();
+    const int target = min_ctas(w);
+    double best = -1e30;
+    Layout pick{};
+    int pick_tx = 0, pick_ty = 0;
+    for (int ty = 1; ty <= std::min(8, ny); ++ty)
+        for (int tx = 1; tx <= std::min(8, nx); ++tx) {
+            Layout L = layout_for(tx, ty, w, s, R, G, PREC_FP32);
+            if (L.bytes > kSmemMax) continue;
+            if (override_kb && L.bytes > override_kb * 1024 && !(tx == 1 && ty == 1)) continue;
+            const int ctas = std::min({228 * 1024 / (L.bytes + 1024), by_regs, by_threads});
+            if (ctas < 1) continue;
+            const int aw = (tx - 1) * s + w, ah = (ty - 1) * s + w;
+            const double blocks_per_win = (double)(aw / G) * (ah / G) / (tx * ty);
+            const double score = std::min(ctas, target) * 1e8 + (double)tx * ty * 1e5 - blocks_per_win * 1e2 -
+                                 std::abs(tx - ty);
+            if (score > best) {
+                best = score;
+                pick = L;
+                pick_tx = tx;
+                pick_ty = ty;
+            }
+        }
+    if (pick_tx == 0) return false;
+    *plan = pick.p;
+    plan->tiles_x = (nx + pick_tx - 1) / pick_tx;
+    plan->tiles_y = (ny + pick_ty - 1) / pick_ty;
+    return true;
+}
+
 bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan)
 {
     if (w < 2 || s < 1 || nx < 1 || ny < 1 || !pass_supported(R, prec)) return false;
     const int G = gcd(w, s);
-    if (prec != PREC_FP32 && (G % 2) != 0) return false;  // paired 16-bit loads need even blocks
+    if (prec == PREC_FP32) return plan_fp32(w, s, R, G, nx, ny, plan);
+    if ((G % 2) != 0) return false;  // paired 16-bit loads need even blocks
     for (int t = 8; t >= 1; --t) {
         const int TX = std::min(t, nx), TY = std::min(t, ny);
         Layout L = layout_for(TX, TY, w, s, R, G, prec);
