@@ -43,15 +43,6 @@ int smem_budget_override()
     return kb;
 }
 
-// Shared memory a tensor-core tile may use (228 KB per SM, 1 KB reserved per
-// CTA), from sweeps of 40..220 KB on GB300 at 16 MP per pass: 72 KB for 8-px
-// blocks, 112 KB for larger blocks, whose windows then share more blocks.
-int smem_budget(int prec, int R, int G)
-{
-    if (const int kb = smem_budget_override()) return kb * 1024;
-    if (prec == PREC_FP32) return (R >= 6 ? 72 : 56) * 1024;
-    return (G >= 16 ? 112 : 72) * 1024;
-}
 constexpr int kSmemMax = 227 * 1024;
 
 // (block, sy, row group) items the FP32 plane loop aims for before it stops
@@ -200,12 +191,13 @@ bool pass_supported(int R, int prec)
     return false;
 }
 
-// CTAs per SM an FP32 tile must leave room for.  Swept on GB300 at 16 MP per
-// pass (targets 2..5): windows of 48 px and more run best at three CTAs, whose
-// larger tiles let neighbouring windows share their blocks (64 px: 0.78 ->
-// 0.59 ms); 24..40 px at four; smaller windows at five.  RPIV_MIN_CTAS
+// CTAs per SM a tile must leave room for.  Swept on GB300 at 16 MP per pass
+// (targets 2..5): FP32 windows of 48 px and more run best at three CTAs,
+// whose larger tiles let neighbouring windows share their blocks (64 px:
+// 0.78 -> 0.59 ms), 24..40 px at four, smaller windows at five; the
+// tensor-core kernel, with its 16-bit copies, at three.  RPIV_MIN_CTAS
 // overrides it (tuning).
-int min_ctas(int w)
+int min_ctas(int w, int prec)
 {
     static int n = [] {
         const char *e = std::getenv("RPIV_MIN_CTAS");
@@ -213,27 +205,28 @@ int min_ctas(int w)
         return (v >= 1 && v <= 8) ? v : 0;
     }();
     if (n) return n;
+    if (prec != PREC_FP32) return 3;
     return w >= 48 ? 3 : (w >= 24 ? 4 : 5);
 }
 
-// FP32 tiles: among shapes of up to 8 x 8 windows (not necessarily square)
-// that leave room for min_ctas() CTAs per SM, counting shared memory (228 KB
-// per SM, 1 KB reserved per CTA), threads and registers (48 per thread, 64
-// for r = 8), the one with the most windows; ties go to fewer blocks per
-// window, then to the squarer tile.  If none fits, the shape with the most
-// CTAs per SM.
-bool plan_fp32(int w, int s, int R, int G, int nx, int ny, PassPlan *plan)
+// Tiles: among shapes of up to 8 x 8 windows (not necessarily square) that
+// leave room for min_ctas() CTAs per SM, counting shared memory (228 KB per
+// SM, 1 KB reserved per CTA), threads and registers (48 per thread; 64 for
+// the FP32 and 80 for the tensor-core kernel at r = 8), the one with the most
+// windows; ties go to fewer blocks per window, then to the squarer tile.  If
+// none fits, the shape with the most CTAs per SM.
+bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
 {
-    const int regs = R >= 8 ? 64 : 48;
+    const int regs = R >= 8 ? (prec == PREC_FP32 ? 64 : 80) : 48;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     const int override_kb = smem_budget_override();
-    const int target = min_ctas(w);
+    const int target = min_ctas(w, prec);
     double best = -1e30;
     Layout pick{};
     int pick_tx = 0, pick_ty = 0;
     for (int ty = 1; ty <= std::min(8, ny); ++ty)
         for (int tx = 1; tx <= std::min(8, nx); ++tx) {
-            Layout L = layout_for(tx, ty, w, s, R, G, PREC_FP32);
+            Layout L = layout_for(tx, ty, w, s, R, G, prec);
             if (L.bytes > kSmemMax) continue;
             if (override_kb && L.bytes > override_kb * 1024 && !(tx == 1 && ty == 1)) continue;
             const int ctas = std::min({228 * 1024 / (L.bytes + 1024), by_regs, by_threads});
@@ -260,19 +253,8 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan)
 {
     if (w < 2 || s < 1 || nx < 1 || ny < 1 || !pass_supported(R, prec)) return false;
     const int G = gcd(w, s);
-    if (prec == PREC_FP32) return plan_fp32(w, s, R, G, nx, ny, plan);
-    if ((G % 2) != 0) return false;  // paired 16-bit loads need even blocks
-    for (int t = 8; t >= 1; --t) {
-        const int TX = std::min(t, nx), TY = std::min(t, ny);
-        Layout L = layout_for(TX, TY, w, s, R, G, prec);
-        if (L.bytes <= smem_budget(prec, R, G) || (t == 1 && L.bytes <= kSmemMax)) {
-            *plan = L.p;
-            plan->tiles_x = (nx + TX - 1) / TX;
-            plan->tiles_y = (ny + TY - 1) / TY;
-            return true;
-        }
-    }
-    return false;
+    if (prec != PREC_FP32 && (G % 2) != 0) return false;  // paired 16-bit loads need even blocks
+    return plan_search(w, s, R, G, nx, ny, prec, plan);
 }
 
 cudaError_t launch_pass(const PassArgs &args, int n_pairs, cudaStream_t st)
