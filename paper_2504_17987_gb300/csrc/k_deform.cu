@@ -20,9 +20,9 @@ namespace rpiv {
 
 namespace {
 
-constexpr int DTX = 64, DTY = 32;  // output pixels per CTA
-constexpr int DROWS = DTY / 4;     // rows per thread (256 threads = 64 columns x 4 row phases)
-constexpr int NODE_CAP = 512;      // nodes a tile can touch (checked on the host)
+constexpr int DTX = 64, DTY = 64;  // output pixels per CTA
+constexpr int DROWS = 8;           // rows per thread and 32-row slice (256 threads = 64 columns x 4 row phases)
+constexpr int NODE_CAP = 640;      // nodes a tile can touch (checked on the host)
 
 __device__ __forceinline__ void axis_weight(int pos, int n, float c0, int s, int &i0, float &t)
 {
@@ -40,24 +40,51 @@ __device__ __forceinline__ void axis_weight(int pos, int n, float c0, int s, int
 }
 
 template <typename T>
-__device__ __forceinline__ float tap(const unsigned char *img, long long pitch, int x, int y)
+__device__ __forceinline__ float tap(const unsigned char *row, int x)
 {
-    return (float)__ldg(reinterpret_cast<const T *>(img + (long long)y * pitch) + x);
+    return (float)__ldg(reinterpret_cast<const T *>(row) + x);
 }
 
+constexpr int NROW_CAP = DTY / 3 + 4;  // node rows a tile touches (steps >= 3, checked on the host)
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The field is bilinear in the nodes: the tile first interpolates every node
+// row it touches along x at each of its columns (cu, cv), so that a pixel
+// needs one interpolation along y.  A tile whose taps provably stay inside
+// the image (its displacement lies within the range of its nodes, a convex
+// combination) skips the clamping; either way every tap is the clamp-to-edge
+// sample.
 template <typename T>
 __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const float *pu, const float *pv,
                             float *out)
 {
     __shared__ float nu[NODE_CAP], nv[NODE_CAP];
-    __shared__ int cix[DTX], riy[DTY];
-    __shared__ float ctx[DTX], rty[DTY];
+    __shared__ float cu[NROW_CAP][DTX], cv[NROW_CAP][DTX];
+    __shared__ int riy[DTY];
+    __shared__ float rty[DTY];
+    __shared__ float red[4][8];
     const int x0 = blockIdx.x * DTX - a.M, y0 = blockIdx.y * DTY - a.M;
     const float c0 = 0.5f * (float)(a.w - 1);
     const bool has = pu != nullptr && pv != nullptr;
-    int ilo = 0, jlo = 0, nwn = 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = threadIdx.x % DTX, ly0 = threadIdx.x / DTX;
+    const int x = x0 + lx;
+    float umin = 0.f, umax = 0.f, vmin = 0.f, vmax = 0.f;
+    bool any_nan = false;
     if (has) {
-        int ihi, jhi;
+        int ilo, ihi, jlo, jhi;
         float t;
         axis_weight(x0, a.nx, c0, a.s, ilo, t);
         axis_weight(x0 + DTX - 1, a.nx, c0, a.s, ihi, t);
@@ -65,73 +92,122 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
         axis_weight(y0 + DTY - 1, a.ny, c0, a.s, jhi, t);
         ihi = min(ihi + 1, a.nx - 1);
         jhi = min(jhi + 1, a.ny - 1);
-        nwn = ihi - ilo + 1;
-        const int nhn = jhi - jlo + 1;
+        const int nwn = ihi - ilo + 1, nhn = jhi - jlo + 1;
+        float lu0 = INFINITY, lu1 = -INFINITY, lv0 = INFINITY, lv1 = -INFINITY;
+        bool nan_seen = false;
         for (int e = threadIdx.x; e < nwn * nhn; e += blockDim.x) {
             const int jj = e / nwn, ii = e - jj * nwn;
-            nu[e] = pu[(jlo + jj) * a.nx + ilo + ii];
-            nv[e] = pv[(jlo + jj) * a.nx + ilo + ii];
+            const float fu = pu[(jlo + jj) * a.nx + ilo + ii], fv = pv[(jlo + jj) * a.nx + ilo + ii];
+            nu[e] = fu;
+            nv[e] = fv;
+            nan_seen |= (fu != fu) || (fv != fv);
+            lu0 = fminf(lu0, fu);
+            lu1 = fmaxf(lu1, fu);
+            lv0 = fminf(lv0, fv);
+            lv1 = fmaxf(lv1, fv);
         }
-        for (int e = threadIdx.x; e < DTX; e += blockDim.x) {
-            int i0;
-            float t;
-            axis_weight(x0 + e, a.nx, c0, a.s, i0, t);
-            cix[e] = i0 - ilo;
-            ctx[e] = t;
+        lu0 = warp_min(lu0);
+        lu1 = warp_max(lu1);
+        lv0 = warp_min(lv0);
+        lv1 = warp_max(lv1);
+        if (lane == 0) {
+            red[0][warp] = lu0;
+            red[1][warp] = lu1;
+            red[2][warp] = lv0;
+            red[3][warp] = lv1;
         }
         for (int e = threadIdx.x; e < DTY; e += blockDim.x) {
             int j0;
-            float t;
             axis_weight(y0 + e, a.ny, c0, a.s, j0, t);
             riy[e] = j0 - jlo;
             rty[e] = t;
         }
+        any_nan = __syncthreads_or(nan_seen);
+        // node rows interpolated along x at this thread's column
+        {
+            int i0;
+            float tx;
+            axis_weight(x, a.nx, c0, a.s, i0, tx);
+            const int ci = i0 - ilo, di = a.nx > 1 ? 1 : 0;
+            for (int jj = ly0; jj < nhn; jj += blockDim.x / DTX) {
+                const float *ru = nu + jj * nwn + ci, *rv = nv + jj * nwn + ci;
+                cu[jj][lx] = ru[0] + tx * (ru[di] - ru[0]);
+                cv[jj][lx] = rv[0] + tx * (rv[di] - rv[0]);
+            }
+        }
+        umin = red[0][0];
+        umax = red[1][0];
+        vmin = red[2][0];
+        vmax = red[3][0];
+        for (int k = 1; k < 8; ++k) {
+            umin = fminf(umin, red[0][k]);
+            umax = fmaxf(umax, red[1][k]);
+            vmin = fminf(vmin, red[2][k]);
+            vmax = fmaxf(vmax, red[3][k]);
+        }
+        // the central warp scales by -1/2 for frame A: the range flips
+        const float su0 = a.scale * umin, su1 = a.scale * umax, sv0 = a.scale * vmin, sv1 = a.scale * vmax;
+        umin = fminf(su0, su1);
+        umax = fmaxf(su0, su1);
+        vmin = fminf(sv0, sv1);
+        vmax = fmaxf(sv0, sv1);
+        __syncthreads();
     }
-    __syncthreads();
-    const int di = a.nx > 1 ? 1 : 0, dj = a.ny > 1 ? 1 : 0;
-    const int lx = threadIdx.x % DTX, ly0 = threadIdx.x / DTX;
-    const int x = x0 + lx;
-    // all rows of a thread are unrolled so that their 4 DROWS gathers are in
-    // flight together; rows and columns past the grown image are computed on
-    // clamped coordinates and not stored
+    // every tap of the tile inside the image, with a pixel to spare against rounding
+    const bool inside = !any_nan && umin > -1048576.f && umax < 1048576.f && vmin > -1048576.f &&
+                        vmax < 1048576.f && x0 + floorf(umin) - 1.f >= 0.f &&
+                        x0 + DTX - 1 + floorf(umax) + 2.f <= (float)(a.W - 1) && y0 + floorf(vmin) - 1.f >= 0.f &&
+                        y0 + DTY - 1 + floorf(vmax) + 2.f <= (float)(a.H - 1);
+    const int dj = a.ny > 1 ? 1 : 0;
+    // the tile in slices of 32 rows; within a slice all rows of a thread are
+    // unrolled so that their gathers are in flight together; rows and columns
+    // past the grown image are computed on clamped coordinates and not stored
+    for (int half = 0; half < DTY / 32; ++half) {
     float res[DROWS];
 #pragma unroll
     for (int k = 0; k < DROWS; ++k) {
-        const int ly = ly0 + 4 * k, y = y0 + ly;
+        const int ly = 32 * half + ly0 + 4 * k, y = y0 + ly;
         float du = 0.f, dv = 0.f;
         if (has) {
-            const int i0 = cix[lx], j0 = riy[ly];
-            const float tx = ctx[lx], ty = rty[ly];
-            const int k00 = j0 * nwn + i0, k01 = k00 + dj * nwn;
-            float t0 = nu[k00] + tx * (nu[k00 + di] - nu[k00]);
-            float t1 = nu[k01] + tx * (nu[k01 + di] - nu[k01]);
-            du = a.scale * (t0 + ty * (t1 - t0));
-            t0 = nv[k00] + tx * (nv[k00 + di] - nv[k00]);
-            t1 = nv[k01] + tx * (nv[k01 + di] - nv[k01]);
-            dv = a.scale * (t0 + ty * (t1 - t0));
+            const int j0 = riy[ly];
+            const float ty = rty[ly];
+            const float u0 = cu[j0][lx], u1 = cu[j0 + dj][lx];
+            const float v0 = cv[j0][lx], v1 = cv[j0 + dj][lx];
+            du = a.scale * (u0 + ty * (u1 - u0));
+            dv = a.scale * (v0 + ty * (v1 - v0));
             // NaN or absurd predictor values are clamped so the index math cannot overflow
             du = fminf(fmaxf(du, -1048576.f), 1048576.f);
             dv = fminf(fmaxf(dv, -1048576.f), 1048576.f);
         }
         const float fx = floorf(du), fy = floorf(dv);
         const float tx = du - fx, ty = dv - fy;
-        const int ix = x + (int)fx, iy = y + (int)fy;
-        const int xa = min(max(ix, 0), a.W - 1), xb = min(max(ix + 1, 0), a.W - 1);
-        const int ya = min(max(iy, 0), a.H - 1), yb = min(max(iy + 1, 0), a.H - 1);
-        const float b00 = tap<T>(img, a.pitch, xa, ya), b10 = tap<T>(img, a.pitch, xb, ya);
-        const float b01 = tap<T>(img, a.pitch, xa, yb), b11 = tap<T>(img, a.pitch, xb, yb);
+        int xa = x + (int)fx, ya = y + (int)fy;
+        int xb = xa + 1, yb = ya + 1;
+        if (!inside) {
+            xb = min(max(xb, 0), a.W - 1);
+            yb = min(max(yb, 0), a.H - 1);
+            xa = min(max(xa, 0), a.W - 1);
+            ya = min(max(ya, 0), a.H - 1);
+        }
+        const unsigned char *rowa = img + (long long)ya * a.pitch, *rowb = img + (long long)yb * a.pitch;
+        const float b00 = tap<T>(rowa, xa), b10 = tap<T>(rowa, xb);
+        const float b01 = tap<T>(rowb, xa), b11 = tap<T>(rowb, xb);
         const float top = b00 + tx * (b10 - b00), bot = b01 + tx * (b11 - b01);
         res[k] = top + ty * (bot - top);
     }
     if (x < a.W + a.M) {
 #pragma unroll
         for (int k = 0; k < DROWS; ++k) {
-            const int y = y0 + ly0 + 4 * k;
+            const int y = y0 + 32 * half + ly0 + 4 * k;
             if (y < a.H + a.M) out[(long long)(y + a.M) * a.out_pitch + (x + a.M)] = res[k];
         }
     }
+    }
 }
 
+// one kernel per pixel type, so that each holds a single copy of the tile's
+// shared arrays
+template <typename T>
 __global__ void __launch_bounds__(256) deform_kernel(const DeformArgs a)
 {
     const int pair = blockIdx.z;
@@ -139,9 +215,7 @@ __global__ void __launch_bounds__(256) deform_kernel(const DeformArgs a)
     const float *pu = (const float *)resolve(a.pred_u, pair);
     const float *pv = (const float *)resolve(a.pred_v, pair);
     float *out = (float *)resolve(a.out, pair);
-    if (a.fmt == PIX_U8) deform_tile<uint8_t>(a, img, pu, pv, out);
-    else if (a.fmt == PIX_U16) deform_tile<uint16_t>(a, img, pu, pv, out);
-    else deform_tile<float>(a, img, pu, pv, out);
+    deform_tile<T>(a, img, pu, pv, out);
 }
 
 }  // namespace
@@ -151,14 +225,16 @@ bool deform_nodes_fit(int w, int s, int nx, int ny)
     (void)w;
     // nodes touched by a DTX x DTY tile along each axis, plus the neighbour node
     const int cx = DTX / s + 3, cy = DTY / s + 3;
-    return std::min(cx, nx) * std::min(cy, ny) <= NODE_CAP;
+    return std::min(cx, nx) * std::min(cy, ny) <= NODE_CAP && std::min(cy, ny) <= NROW_CAP;
 }
 
 cudaError_t launch_deform(const DeformArgs &a, int n_pairs, cudaStream_t st)
 {
     const int WE = a.W + 2 * a.M, HE = a.H + 2 * a.M;
     dim3 grid((WE + DTX - 1) / DTX, (HE + DTY - 1) / DTY, n_pairs);
-    deform_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.fmt == PIX_U8) deform_kernel<uint8_t><<<grid, 256, 0, st>>>(a);
+    else if (a.fmt == PIX_U16) deform_kernel<uint16_t><<<grid, 256, 0, st>>>(a);
+    else deform_kernel<float><<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
