@@ -289,7 +289,7 @@ class GpuExecutor(Executor):
     CUDA stream per slot, so batches in different slots overlap."""
 
     def __init__(self, slots: int, precision: str = "bf16", max_batch: int = 64, cold_batch: int = 8,
-                 device: int = 0, max_megapixels: float = 16.0):
+                 device: int = 0, max_megapixels: float = 16.0, prewarm: bool = False):
         import torch
         self.torch = torch
         self.precision = precision
@@ -298,6 +298,9 @@ class GpuExecutor(Executor):
         # pixels per launch are capped so that a batch of large frames holds
         # the GPU for about as long as a batch of small ones (tail latency)
         self.max_megapixels = max_megapixels
+        # capture every batch size's graph when an engine is created, so that
+        # no request waits for a first-use capture
+        self.prewarm = prewarm
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.engines = {}
@@ -321,8 +324,27 @@ class GpuExecutor(Executor):
         from .binding import Engine
         k = (key, mode, slot)
         if k not in self.engines:
-            self.engines[k] = Engine(self._cfg(key, mode), device=self.device)
+            eng = Engine(self._cfg(key, mode), device=self.device)
+            self.engines[k] = eng
+            if self.prewarm:
+                self._prewarm(eng, key, mode, slot)
         return self.engines[k]
+
+    def _prewarm(self, eng, key: Key, mode: str, slot: int):
+        torch = self.torch
+        W, H, bits = key
+        dt = torch.uint8 if bits == 8 else torch.int16
+        st = self.streams[slot]
+        with torch.cuda.stream(st):
+            a = torch.zeros((H, W), dtype=dt, device=self.device)
+            pu = torch.zeros((eng.ny, eng.nx), dtype=torch.float32, device=self.device)
+            for n in range(1, self.max_pairs(key, mode) + 1):
+                outs = eng.empty_outputs(n)
+                if n == 1:
+                    outs = tuple(o.unsqueeze(0) for o in outs)
+                preds = [(pu, pu)] * n if mode == WARM else None
+                eng.process_batch([a] * n, [a] * n, preds=preds, outs=outs, stream=st)
+        st.synchronize()
 
     def engine_bytes(self, key: Key, mode: str) -> int:
         W, H, bits = key
