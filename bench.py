@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--latency-requests", type=int, default=200)
     p.add_argument("--workload", default="paper_1mp", choices=["paper_1mp", "paper_1mp_r1"],
                    help="paper_1mp_r1: the paper's 16 px / +-1 operating point on the same images")
-    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve", "precision", "adjoint"],
+    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve", "precision", "adjoint", "sizes"],
                    help="ncu: one warm-up step and one step of the headline path, nothing else (profiler runs); "
                         "serve: the streaming mix (Poisson arrivals over camera streams); "
                         "precision: the 8 MP Fourier-mode pair, FP32/BF16/FP16 fields against the FP64 oracle")
@@ -315,6 +315,56 @@ def run_precision(args):
     return 0
 
 
+# ------------------------------------------------------------ size sweep --
+
+SWEEP_SIZES = [(512, 512), (768, 640), (1024, 1024), (1600, 1200), (2048, 2048), (3840, 2160), (4096, 4096),
+               (8192, 4096)]
+
+
+def run_sizes(args):
+    """Frames per second against image size (0.26 .. 33.6 MP) for the paper's
+    16 px / 50 % operating point (pyramid, 32 px +-4, then 16 px +-1), the
+    shape of the paper's throughput-against-size figure (Sec. 4.1).  Batches
+    hold about 64 MP."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_17987_gb300 as rp
+    from synth import workloads as wl
+    sched = wl.paper_1mp_r1().schedule
+    rows = []
+    for (W, H) in SWEEP_SIZES:
+        wk = wl.paper_1mp(seed=1002, W=W, H=H)
+        A, B = wk.render()
+        a, b = rp.to_device(A), rp.to_device(B)
+        n = max(1, min(64, int(64e6 // (W * H))))
+        cfg = rp.Config.from_schedule(W, H, sched, bit_depth=12, precision=args.headline, max_batch=n)
+        eng = rp.Engine(cfg)
+        outs = eng.empty_outputs(n)
+        if n == 1:
+            outs = tuple(o.unsqueeze(0) for o in outs)
+        for _ in range(3):
+            eng.process_batch([a] * n, [b] * n, outs=outs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        steps = 10
+        for _ in range(steps):
+            eng.process_batch([a] * n, [b] * n, outs=outs)
+        e1.record()
+        torch.cuda.synchronize()
+        fps = n * steps / (e0.elapsed_time(e1) / 1000.0)
+        rows.append({"width": W, "height": H, "megapixels": W * H / 1e6, "batch": n, "pairs_per_s": fps,
+                     "megapixels_per_s": fps * W * H / 1e6, "vectors": eng.nx * eng.ny})
+        eng.close()
+        del a, b, outs
+        torch.cuda.empty_cache()
+    print(json.dumps({"mode": "sizes", "precision": args.headline, "workload": WORKLOAD_R1, "rows": rows,
+                      "data": "synthetic"}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------ differentiation --
 
 def run_adjoint(args):
@@ -434,6 +484,8 @@ def main():
         return run_precision(args)
     if args.mode == "adjoint":
         return run_adjoint(args)
+    if args.mode == "sizes":
+        return run_sizes(args)
     if args.mode == "serve":
         import numpy as np  # noqa: F811
         globals()["np"] = np

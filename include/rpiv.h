@@ -269,6 +269,15 @@ rpiv_status rpiv_stage_vorticity(const float *u, const float *v, int nx, int ny,
 rpiv_status rpiv_stage_downsample(const void *img, size_t pitch_bytes, int fmt, int width, int height,
                                   float *out, void *cuda_stream);
 
+/* Exponential smoothing in time (paper Sec. 2: the optical-flow estimate is
+ * smoothed with a constant alpha_1 before it predicts, and the sub-pixel
+ * field with alpha_2 before it is output):
+ *     state[i] = init ? x[i] : alpha * x[i] + (1 - alpha) * state[i]
+ * over n floats of device memory, in FP32.  x and state may not overlap
+ * unless they are the same array.  Errors: INVALID_ARG (null pointers with
+ * n > 0, alpha outside [0, 1]), CUDA.                                       */
+rpiv_status rpiv_stage_ema(const float *x, float *state, size_t n, float alpha, int init, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

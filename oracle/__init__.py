@@ -22,6 +22,8 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   downsample             pinned: affine images, constant images
   vorticity              pinned: solid-body rotation, Lamb-Oseen bound
   score_grad             pinned: central finite differences
+  ema                    pinned: alpha 0 and 1, the geometric closed form of a
+                         constant input, the step response
   process_pair           pinned: imposed uniform shifts (<= 0.02 px), zero
                          displacement, vortex field against its analytic truth
 """
@@ -258,6 +260,16 @@ def vorticity(u, v, s: int) -> np.ndarray:
     w = np.empty_like(u)
     lib().orc_vorticity(_d(u), _d(v), nx, ny, s, _d(w))
     return w
+
+
+def ema(x, state, alpha: float, init: bool = False) -> np.ndarray:
+    """Exponential smoothing in time (Sec. 2, constants alpha_1 for the
+    predictor and alpha_2 for the output): the new state is x on the first
+    frame, else alpha * x + (1 - alpha) * state."""
+    x = _f64(x)
+    if init:
+        return x.copy()
+    return alpha * x + (1.0 - alpha) * _f64(state)
 
 
 def score_grad(A, B, w: int, s: int, gu, gv, grad: bool = True):

@@ -27,8 +27,8 @@ EXPORTED = sorted(["rpiv_config_default", "rpiv_validate_config", "rpiv_create",
                    "rpiv_workspace_bytes", "rpiv_process_pair", "rpiv_process_batch", "rpiv_backward", "rpiv_wait",
                    "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes",
                    "rpiv_stage_correlate_noalloc", "rpiv_stage_validate",
-                   "rpiv_stage_interp", "rpiv_stage_vorticity", "rpiv_stage_downsample", "rpiv_trace_enable",
-                   "rpiv_trace_read"])
+                   "rpiv_stage_interp", "rpiv_stage_vorticity", "rpiv_stage_downsample", "rpiv_stage_ema",
+                   "rpiv_trace_enable", "rpiv_trace_read"])
 
 
 class RpivError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
     L.rpiv_stage_validate.argtypes = [vp, vp, vp, i32, i32, f32, f32, i32, vp, vp, vp, vp]
     L.rpiv_stage_interp.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp]
     L.rpiv_stage_vorticity.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+    L.rpiv_stage_ema.argtypes = [vp, vp, sz, ctypes.c_float, i32, vp]
     L.rpiv_stage_downsample.argtypes = [vp, sz, i32, i32, i32, vp, vp]
     L.rpiv_trace_enable.argtypes = [vp, i32]
     L.rpiv_trace_read.argtypes = [vp, ctypes.POINTER(TraceRecord), i32, ctypes.POINTER(i32)]
@@ -370,6 +371,16 @@ def stage_vorticity(u, v, s: int, stream=None):
     o = torch.empty_like(u)
     _check(load().rpiv_stage_vorticity(_ptr(u), _ptr(v), nx, ny, s, _ptr(o), _stream(stream)))
     return o
+
+
+def stage_ema(x, state, alpha: float, init: bool = False, stream=None):
+    """state <- x (init) or alpha x + (1 - alpha) state, in place; returns state."""
+    if x.dtype != torch.float32 or state.dtype != torch.float32 or x.numel() != state.numel():
+        raise ValueError("x and state: float32 tensors of the same size")
+    if not (x.is_contiguous() and state.is_contiguous()):
+        raise ValueError("x and state must be contiguous")
+    _check(load().rpiv_stage_ema(_ptr(x), _ptr(state), x.numel(), float(alpha), 1 if init else 0, _stream(stream)))
+    return state
 
 
 def stage_downsample(img, stream=None):

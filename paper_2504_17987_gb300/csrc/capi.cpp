@@ -1071,6 +1071,15 @@ rpiv_status rpiv_stage_vorticity(const float *u, const float *v, int nx, int ny,
     return RPIV_OK;
 }
 
+rpiv_status rpiv_stage_ema(const float *x, float *state, size_t n, float alpha, int init, void *cuda_stream)
+{
+    if (n > 0 && (!x || !state)) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if (!(alpha >= 0.f && alpha <= 1.f)) return fail(RPIV_ERR_INVALID_ARG, "alpha must be in [0, 1]");
+    if (x != state && x < state + n && state < x + n) return fail(RPIV_ERR_INVALID_ARG, "x and state overlap");
+    CK(launch_ema(x, state, n, alpha, init, static_cast<cudaStream_t>(cuda_stream)), "smoothing launch");
+    return RPIV_OK;
+}
+
 rpiv_status rpiv_stage_downsample(const void *img, size_t pitch_bytes, int fmt, int width, int height, float *out,
                                   void *cuda_stream)
 {

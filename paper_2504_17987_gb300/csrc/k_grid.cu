@@ -4,6 +4,7 @@
 //   - grid-to-grid bilinear interpolation (pass-to-pass predictor, pyramid)
 //   - vorticity omega = dv/dx - du/dy (paper Sec. 1-2, displayed field)
 //   - 2x2 box downsampling of the image pyramid (coarse-to-fine predictor)
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -270,6 +271,22 @@ __global__ void vort_kernel(const VortArgs a)
         else dudy = (u[(j + 1) * nx + i] - u[(j - 1) * nx + i]) / (2.f * s);
     }
     o[k] = dvdx - dudy;
+}
+
+__global__ void ema_kernel(const float *__restrict__ x, float *state, size_t n, float alpha, int init)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float xi = x[i];
+        state[i] = init ? xi : alpha * xi + (1.f - alpha) * state[i];
+    }
+}
+
+cudaError_t launch_ema(const float *x, float *state, size_t n, float alpha, int init, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 8);
+    ema_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, state, n, alpha, init);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vort(const VortArgs &a, int n_pairs, cudaStream_t st)

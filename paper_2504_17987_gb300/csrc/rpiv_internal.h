@@ -179,6 +179,9 @@ struct VortArgs {
 };
 cudaError_t launch_vort(const VortArgs &a, int n_pairs, cudaStream_t st);
 
+// state = init ? x : alpha x + (1 - alpha) state, elementwise over n floats.
+cudaError_t launch_ema(const float *x, float *state, size_t n, float alpha, int init, cudaStream_t st);
+
 struct DownArgs {
     PtrRef src;
     int fmt;

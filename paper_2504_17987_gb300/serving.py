@@ -289,7 +289,7 @@ class GpuExecutor(Executor):
     CUDA stream per slot, so batches in different slots overlap."""
 
     def __init__(self, slots: int, precision: str = "bf16", max_batch: int = 64, cold_batch: int = 8,
-                 device: int = 0, max_megapixels: float = 16.0, prewarm: bool = False):
+                 device: int = 0, max_megapixels: float = 16.0, prewarm: bool = False, alpha1=None, alpha2=None):
         import torch
         self.torch = torch
         self.precision = precision
@@ -301,6 +301,13 @@ class GpuExecutor(Executor):
         # capture every batch size's graph when an engine is created, so that
         # no request waits for a first-use capture
         self.prewarm = prewarm
+        # exponential smoothing in time (paper Sec. 2): alpha1 on the field a
+        # stream passes on as its next predictor, alpha2 on the field it
+        # outputs; None leaves the field as measured
+        self.alpha1 = alpha1
+        self.alpha2 = alpha2
+        self.pred_state = {}
+        self.out_state = {}
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.engines = {}
@@ -377,20 +384,53 @@ class GpuExecutor(Executor):
                     pr[0].record_stream(st)
                     pr[1].record_stream(st)
             eng.process_batch(a, b, preds=p, outs=outs, stream=st)
+            smoothed = self._smooth(reqs, outs, st)
             ev = torch.cuda.Event()
             ev.record(st)
-        return (ev, outs, a, b, p)
+        return (ev, outs, a, b, p, smoothed)
+
+    def _smooth(self, reqs, outs, st):
+        """Per request: the next predictor alpha1 x + (1 - alpha1) previous
+        predictor (from a copy of the measured field), then the output
+        alpha2 x + (1 - alpha2) previous output, in place; a stream's first
+        frame starts both states."""
+        from .binding import stage_ema
+        preds = []
+        for i, r in enumerate(reqs):
+            nxt = None
+            if self.alpha1 is not None:
+                nxt = (outs[0][i].clone(), outs[1][i].clone())
+                prev = self.pred_state.get(r.stream)
+                if prev is not None:
+                    for k in range(2):
+                        prev[k].record_stream(st)
+                        stage_ema(prev[k], nxt[k], 1.0 - self.alpha1, stream=st)
+            preds.append(nxt)
+            if self.alpha2 is not None:
+                prev = self.out_state.get(r.stream)
+                if prev is not None:
+                    for k in range(3):
+                        prev[k].record_stream(st)
+                        stage_ema(prev[k], outs[k][i], 1.0 - self.alpha2, stream=st)
+        return preds
 
     def poll(self, token) -> bool:
         return token[0].query()
 
     def collect(self, token, reqs):
-        outs = token[1]
+        outs, smoothed = token[1], token[5]
         u, v, w, m = outs
         for i, r in enumerate(reqs):
             r.result = (u[i], v[i], w[i], m[i])
+            if r.error is None:
+                if self.alpha1 is not None:
+                    self.pred_state[r.stream] = smoothed[i]
+                if self.alpha2 is not None:
+                    self.out_state[r.stream] = (u[i], v[i], w[i])
 
     def field_of(self, req):
+        if self.alpha1 is not None and req.stream in self.pred_state:
+            return self.pred_state[req.stream]
         return (req.result[0], req.result[1])
 
     def close(self):

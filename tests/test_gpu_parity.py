@@ -281,3 +281,37 @@ def test_pipeline_bf16_within_0p01_px():
     ref = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels)
     err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
     assert np.percentile(err, 99) <= 0.01, f"p99 {np.percentile(err, 99):.4f}"
+
+
+def test_pipeline_paper_exact_variant_central_warp_zero_radius():
+    """The paper's own correction (Sec. 2): both frames warped by central
+    differences and the 5-point stencil fixed at the predicted peak (r = 0),
+    after a pyramid and a 32 px +-4 pass; end to end against the oracle."""
+    w = wl.paper_1mp(W=512, H=384)
+    A, B = w.render()
+    sc = wl.Schedule((32, 16), (0.5, 0.5), (4, 0), levels=2)
+    H, W = A.shape
+    cfg = rp.Config.from_schedule(W, H, sc, bit_depth=12, deform="central")
+    eng = rp.Engine(cfg)
+    u, v, om, m = [t.cpu().numpy() for t in eng.process_pair(dev(A), dev(B))]
+    eng.close()
+    ref = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels, deform="central")
+    err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
+    assert np.mean(err <= TOL_PX) >= 0.99, f"within 1e-3: {np.mean(err <= TOL_PX):.4f}"
+    assert np.percentile(err, 99) <= 0.05
+    assert np.mean(m == ref.mask) >= 0.99
+
+
+def test_ema_stage_matches_oracle():
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(10007).astype(np.float32)
+    st = rng.standard_normal(10007).astype(np.float32)
+    tx, ts = torch.from_numpy(x).cuda(), torch.from_numpy(st).cuda()
+    for alpha in (0.0, 0.25, 0.5, 1.0):
+        out = rp.stage_ema(tx, ts.clone(), alpha).cpu().numpy()
+        ref = oracle.ema(x, st, alpha)
+        assert np.abs(out - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+    out = rp.stage_ema(tx, ts.clone(), 0.5, init=True).cpu().numpy()
+    assert np.array_equal(out, x)
+    with pytest.raises(rp.RpivError):
+        rp.stage_ema(tx, ts.clone(), 1.5)

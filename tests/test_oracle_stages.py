@@ -324,3 +324,21 @@ def test_sampled_window_evaluation_equals_the_full_pass():
     assert np.array_equal(part.u[m], full.u[m]) and np.array_equal(part.v[m], full.v[m])
     assert np.array_equal(part.peaks[m], full.peaks[m]) and np.array_equal(part.plane[m], full.plane[m])
     assert np.all(part.valid[~m] == -1) and np.all(np.isnan(part.u[~m]))
+
+
+def test_ema_special_cases_and_closed_form():
+    rng = np.random.default_rng(12)
+    x, s0 = rng.standard_normal(50), rng.standard_normal(50)
+    assert np.array_equal(oracle.ema(x, s0, 1.0), x)
+    assert np.array_equal(oracle.ema(x, s0, 0.0), s0)
+    assert np.array_equal(oracle.ema(x, s0, 0.3, init=True), x)
+    # a constant input: s_k = x + (1 - a)^k (s_0 - x)
+    a, s = 0.35, s0.copy()
+    for k in range(1, 9):
+        s = oracle.ema(x, s, a)
+        assert np.allclose(s, x + (1 - a) ** k * (s0 - x), rtol=0, atol=1e-12)
+    # step response from zero: 1 - (1 - a)^k
+    s = np.zeros(1)
+    for k in range(1, 6):
+        s = oracle.ema(np.ones(1), s, a)
+    assert abs(s[0] - (1 - (1 - a) ** 5)) <= 1e-15

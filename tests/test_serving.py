@@ -217,3 +217,46 @@ def test_gpu_mix_results_equal_alone_results():
         assert torch.equal(w, r.result[2]) and torch.equal(m, r.result[3]), r.rid
         eng.close()
     ex.close()
+
+
+@pytest.mark.gpu
+def test_gpu_temporal_smoothing_follows_the_recurrence():
+    """alpha1 on the predictor a stream passes on, alpha2 on its output: the
+    served fields equal the recurrence run frame by frame through the engine."""
+    import torch
+    import paper_2504_17987_gb300 as rp
+    import synth
+    from paper_2504_17987_gb300 import build
+    build.build()
+    W, H, bits = 256, 256, 8
+    n_streams, frames, a1, a2 = 3, 4, 0.5, 0.25
+    reqs, k = [], 0
+    for f in range(frames):
+        for s in range(n_streams):
+            spec = synth.ImageSpec(W=W, H=H, bit_depth=bits, ppp=0.05, dp=(2.5, 2.5), seed=9100 + 31 * s + f)
+            A, B = synth.render_pair(spec, wl.serving_stream_flow(s, f, W, H))
+            reqs.append(sv.Request(rid=k, stream=s, frame=f, arrival=0.0, key=(W, H, bits),
+                                   payload=(rp.to_device(A, pin=True), rp.to_device(B, pin=True))))
+            k += 1
+    ex = sv.GpuExecutor(slots=2, precision="fp32", max_batch=4, cold_batch=2, alpha1=a1, alpha2=a2)
+    sch = sv.Scheduler(ex, max_batch=4, slots=2, hbm_budget=4e9)
+    rep = sch.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    assert rep["requests"] == len(reqs)
+    for s in range(n_streams):
+        mine = sorted((r for r in sch.done if r.stream == s), key=lambda r: r.frame)
+        pred = out = None
+        for r in mine:
+            cfg = (sv.warm_config if r.mode == sv.WARM else sv.cold_config)(W, H, bits, "fp32", 1)
+            eng = rp.Engine(cfg)
+            raw = [t.clone() for t in eng.process_pair(r.payload[0].cuda(), r.payload[1].cuda(), pred=pred)]
+            torch.cuda.synchronize()
+            eng.close()
+            new_pred = (raw[0].clone(), raw[1].clone())
+            if pred is not None:
+                new_pred = (a1 * raw[0] + (1 - a1) * pred[0], a1 * raw[1] + (1 - a1) * pred[1])
+            new_out = raw[:3] if out is None else [a2 * raw[i] + (1 - a2) * out[i] for i in range(3)]
+            for i in range(3):
+                assert torch.allclose(r.result[i], new_out[i], rtol=1e-5, atol=1e-5), (s, r.frame, i)
+            pred, out = new_pred, new_out
+    ex.close()
