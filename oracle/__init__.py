@@ -24,6 +24,9 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   score_grad             pinned: central finite differences
   ema                    pinned: alpha 0 and 1, the geometric closed form of a
                          constant input, the step response
+  preprocess             pinned: constant and affine images (high-pass zero
+                         inside), global histogram equalisation of a uniform
+                         histogram, the clipped constant image in closed form
   process_pair           pinned: imposed uniform shifts (<= 0.02 px), zero
                          displacement, vortex field against its analytic truth
 """
@@ -96,6 +99,9 @@ def lib():
         L.orc_downsample.restype = None
         L.orc_vorticity.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         L.orc_vorticity.restype = None
+        L.orc_preprocess.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, _dp]
+        L.orc_preprocess.restype = None
         L.orc_score_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                      _dp, _dp]
         L.orc_score_grad.restype = ctypes.c_double
@@ -260,6 +266,16 @@ def vorticity(u, v, s: int) -> np.ndarray:
     w = np.empty_like(u)
     lib().orc_vorticity(_d(u), _d(v), nx, ny, s, _d(w))
     return w
+
+
+def preprocess(img, vmax: int, hp: int = 7, tiles=(8, 8), clip_pct: int = 200) -> np.ndarray:
+    """High-pass filter and CLAHE before the flow estimate (Sec. 2); the
+    readings are stated in rpiv_oracle.c.  Returns a float image in [0, vmax]."""
+    I = _f64(img)
+    H, W = I.shape
+    out = np.empty((H, W))
+    lib().orc_preprocess(_d(I), W, H, int(vmax), int(hp), int(tiles[0]), int(tiles[1]), int(clip_pct), _d(out))
+    return out
 
 
 def ema(x, state, alpha: float, init: bool = False) -> np.ndarray:

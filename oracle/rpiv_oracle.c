@@ -544,3 +544,123 @@ double orc_score_grad(const double *A, const double *B, int W, int H, int w, int
     free(gyb);
     return S;
 }
+
+/* ------------------------------------------------------- pre-processing --- */
+/*
+ * The pre-processing before the flow estimate (Sec. 2): a high-pass filter
+ * against the static background, then contrast-limited adaptive histogram
+ * equalisation (CLAHE, Zuiderveld 1994).  Readings (the paper gives no
+ * parameters):
+ *   high-pass   d(x) = max(0, n I(x) - S(x)), S the sum of I over the
+ *               (2 hp + 1)^2 box around x with clamp-to-edge, n its pixel
+ *               count; the filtered value is d / n (I minus its box mean,
+ *               negative values cut at zero).  hp = 0 disables it (d / n = I).
+ *   CLAHE       tiles tx x ty of ceil(W / tx) x ceil(H / ty) pixels (the last
+ *               row and column of tiles may be smaller); 256 bins over
+ *               [0, vmax + 1): bin = floor(d * 256 / (n (vmax + 1)));
+ *               per tile of N pixels the histogram is clipped at
+ *               L = max(1, floor(clip_pct N / (100 * 256))), the clipped
+ *               excess E is spread as E / 256 to every bin plus one to the
+ *               first E mod 256 bins; map[b] = cdf[b] * vmax / N.
+ *               A pixel takes the bilinear blend of the maps of the four
+ *               tiles whose centres surround it (centres at t * tw +
+ *               (width_t - 1) / 2; clamped to the outer centres).
+ *               clip_pct = 0 disables CLAHE (output d / n).
+ * Every integer is computed exactly (64-bit), so the bins are the kernel's.
+ */
+static long long clamp_ll(long long v, long long lo, long long hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+void orc_preprocess(const double *I, int W, int H, int vmax, int hp, int tx, int ty, int clip_pct, double *out)
+{
+    const long long n = (long long)(2 * hp + 1) * (2 * hp + 1);
+    long long *d = (long long *)malloc(sizeof(long long) * (size_t)W * H);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            long long S = 0;
+            for (int dy = -hp; dy <= hp; ++dy)
+                for (int dx = -hp; dx <= hp; ++dx)
+                    S += (long long)I[clamp_ll(y + dy, 0, H - 1) * W + clamp_ll(x + dx, 0, W - 1)];
+            long long v = hp > 0 ? n * (long long)I[(size_t)y * W + x] - S : (long long)I[(size_t)y * W + x];
+            d[(size_t)y * W + x] = v > 0 ? v : 0;
+        }
+    if (clip_pct <= 0) {
+        for (size_t i = 0; i < (size_t)W * H; ++i) out[i] = (double)d[i] / (double)n;
+        free(d);
+        return;
+    }
+    const int nb = 256;
+    const int tw = (W + tx - 1) / tx, th = (H + ty - 1) / ty;
+    double *map = (double *)malloc(sizeof(double) * (size_t)tx * ty * nb);
+    const long long den = n * ((long long)vmax + 1);
+    for (int j = 0; j < ty; ++j)
+        for (int i = 0; i < tx; ++i) {
+            long long h[256] = {0};
+            const int x0 = i * tw, x1 = (x0 + tw < W) ? x0 + tw : W;
+            const int y0 = j * th, y1 = (y0 + th < H) ? y0 + th : H;
+            long long N = 0;
+            for (int y = y0; y < y1; ++y)
+                for (int x = x0; x < x1; ++x) {
+                    long long b = d[(size_t)y * W + x] * nb / den;
+                    if (b > nb - 1) b = nb - 1;
+                    h[b]++;
+                    N++;
+                }
+            long long L = (long long)clip_pct * N / (100LL * nb);
+            if (L < 1) L = 1;
+            long long E = 0;
+            for (int b = 0; b < nb; ++b)
+                if (h[b] > L) {
+                    E += h[b] - L;
+                    h[b] = L;
+                }
+            long long c = 0;
+            for (int b = 0; b < nb; ++b) {
+                c += h[b] + E / nb + (b < E % nb ? 1 : 0);
+                map[((size_t)j * tx + i) * nb + b] = N > 0 ? (double)c * vmax / (double)N : 0.0;
+            }
+        }
+    for (int y = 0; y < H; ++y) {
+        /* vertical tile pair and weight */
+        int j0, j1;
+        double wy;
+        {
+            const double cy0 = (th - 1) * 0.5;
+            const int jl = ty - 1;
+            const double cyl = jl * th + ((H - jl * th) - 1) * 0.5;
+            if (ty == 1 || y <= cy0) { j0 = j1 = 0; wy = 0.0; }
+            else if (y >= cyl) { j0 = j1 = jl; wy = 0.0; }
+            else {
+                j0 = (int)floor((y - cy0) / th);
+                if (j0 > ty - 2) j0 = ty - 2;
+                j1 = j0 + 1;
+                const double c0 = j0 * th + (th - 1) * 0.5;
+                const double c1 = (j1 == jl) ? cyl : j1 * th + (th - 1) * 0.5;
+                wy = (y - c0) / (c1 - c0);
+            }
+        }
+        for (int x = 0; x < W; ++x) {
+            int i0, i1;
+            double wx;
+            const double cx0 = (tw - 1) * 0.5;
+            const int il = tx - 1;
+            const double cxl = il * tw + ((W - il * tw) - 1) * 0.5;
+            if (tx == 1 || x <= cx0) { i0 = i1 = 0; wx = 0.0; }
+            else if (x >= cxl) { i0 = i1 = il; wx = 0.0; }
+            else {
+                i0 = (int)floor((x - cx0) / tw);
+                if (i0 > tx - 2) i0 = tx - 2;
+                i1 = i0 + 1;
+                const double c0 = i0 * tw + (tw - 1) * 0.5;
+                const double c1 = (i1 == il) ? cxl : i1 * tw + (tw - 1) * 0.5;
+                wx = (x - c0) / (c1 - c0);
+            }
+            long long b = d[(size_t)y * W + x] * nb / den;
+            if (b > nb - 1) b = nb - 1;
+            const double m00 = map[((size_t)j0 * tx + i0) * nb + b], m01 = map[((size_t)j0 * tx + i1) * nb + b];
+            const double m10 = map[((size_t)j1 * tx + i0) * nb + b], m11 = map[((size_t)j1 * tx + i1) * nb + b];
+            out[(size_t)y * W + x] = (1 - wy) * ((1 - wx) * m00 + wx * m01) + wy * ((1 - wx) * m10 + wx * m11);
+        }
+    }
+    free(map);
+    free(d);
+}

@@ -342,3 +342,64 @@ def test_ema_special_cases_and_closed_form():
     for k in range(1, 6):
         s = oracle.ema(np.ones(1), s, a)
     assert abs(s[0] - (1 - (1 - a) ** 5)) <= 1e-15
+
+
+def _clahe_constant_closed_form(N, vmax, clip_pct):
+    L = max(1, clip_pct * N // (100 * 256))
+    E = N - L
+    c0 = L + E // 256 + (1 if E % 256 > 0 else 0)
+    return c0 * vmax / N
+
+
+@pytest.mark.parametrize("W,H,tiles,clip", [(16, 16, (2, 2), 200), (40, 24, (4, 3), 300), (64, 64, (1, 1), 50000)])
+def test_preprocess_constant_image_closed_form(W, H, tiles, clip):
+    img = np.full((H, W), 1234.0)
+    out = oracle.preprocess(img, 4095, hp=3, tiles=tiles, clip_pct=clip)
+    # the high-pass leaves zero everywhere: every pixel falls in bin 0 of every tile
+    tw, th = -(-W // tiles[0]), -(-H // tiles[1])
+    for j in range(tiles[1]):
+        for i in range(tiles[0]):
+            N = (min(W, (i + 1) * tw) - i * tw) * (min(H, (j + 1) * th) - j * th)
+            cy = j * th + (min(H, (j + 1) * th) - j * th - 1) // 2
+            cx = i * tw + (min(W, (i + 1) * tw) - i * tw - 1) // 2
+            if (min(W, (i + 1) * tw) - i * tw) % 2 == 1 and (min(H, (j + 1) * th) - j * th) % 2 == 1:
+                # at a tile's own centre only its map contributes
+                assert abs(out[cy, cx] - _clahe_constant_closed_form(N, 4095, clip)) <= 1e-12
+
+
+def test_preprocess_highpass_removes_affine_background_and_identity():
+    H, W = 40, 48
+    Y, X = np.mgrid[0:H, 0:W]
+    ramp = 30.0 + 2.0 * X + 3.0 * Y
+    out = oracle.preprocess(ramp, 4095, hp=4, tiles=(1, 1), clip_pct=0)
+    # the box mean of an affine image is its centre value: zero away from the borders
+    assert np.all(out[4:-4, 4:-4] == 0.0)
+    # hp = 0 and no CLAHE: the identity
+    rng = np.random.default_rng(8)
+    img = rng.integers(0, 4096, (H, W)).astype(np.float64)
+    assert np.array_equal(oracle.preprocess(img, 4095, hp=0, tiles=(1, 1), clip_pct=0), img)
+
+
+def test_preprocess_uniform_histogram_is_equalised_globally():
+    # one tile, a clip limit above every count: plain histogram equalisation
+    vmax = 255
+    vals = np.repeat(np.arange(256, dtype=np.float64), 16).reshape(64, 64)
+    out = oracle.preprocess(vals, vmax, hp=0, tiles=(1, 1), clip_pct=10 ** 6)
+    # 16 pixels per bin: cdf(b) = 16 (b + 1), map = cdf vmax / N
+    assert np.allclose(out, (vals + 1) / 256.0 * vmax, rtol=0, atol=1e-12)
+
+
+def test_preprocess_tile_maps_blend_bilinearly_between_centres():
+    # two tiles side by side with different constant content: pixels at the
+    # centres take their own tile's map, halfway between them the mean
+    W, H = 32, 9
+    img = np.zeros((H, W))
+    img[:, 16:] = 200.0
+    rng = np.random.default_rng(3)
+    img += rng.integers(0, 2, (H, W))  # two levels per tile
+    out = oracle.preprocess(img, 255, hp=0, tiles=(2, 1), clip_pct=10 ** 6)
+    left = oracle.preprocess(img[:, :16], 255, hp=0, tiles=(1, 1), clip_pct=10 ** 6)
+    right = oracle.preprocess(img[:, 16:], 255, hp=0, tiles=(1, 1), clip_pct=10 ** 6)
+    # centres at x = 7.5 and 23.5 (even widths): x <= 7.5 uses the left map alone
+    assert np.allclose(out[:, :8], left[:, :8], atol=1e-12)
+    assert np.allclose(out[:, 24:], right[:, 8:], atol=1e-12)
