@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--latency-requests", type=int, default=200)
     p.add_argument("--workload", default="paper_1mp", choices=["paper_1mp", "paper_1mp_r1"],
                    help="paper_1mp_r1: the paper's 16 px / +-1 operating point on the same images")
-    p.add_argument("--mode", default="full", choices=["full", "ncu", "serve", "precision", "adjoint", "sizes"],
+    p.add_argument("--mode", default="full",
+                   choices=["full", "ncu", "serve", "precision", "adjoint", "sizes", "preprocess"],
                    help="ncu: one warm-up step and one step of the headline path, nothing else (profiler runs); "
                         "serve: the streaming mix (Poisson arrivals over camera streams); "
                         "precision: the 8 MP Fourier-mode pair, FP32/BF16/FP16 fields against the FP64 oracle")
@@ -315,6 +316,53 @@ def run_precision(args):
     return 0
 
 
+# -------------------------------------------------------- pre-processing --
+
+def run_preprocess(args):
+    """High-pass (15 x 15 box) and CLAHE (8 x 8 tiles, clip 2) of both frames of
+    a 1 MP 12-bit pair, then the correction path on the float frames: time per
+    pair of each."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_17987_gb300 as rp
+    from synth import workloads as wl
+    wk = wl.paper_1mp()
+    A, B = wk.render()
+    H, W = A.shape
+    a, b = rp.to_device(A), rp.to_device(B)
+
+    def pre():
+        return (rp.stage_preprocess(a, 4095, hp=7, tiles=(8, 8), clip_pct=200),
+                rp.stage_preprocess(b, 4095, hp=7, tiles=(8, 8), clip_pct=200))
+    for _ in range(3):
+        pa, pb = pre()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        pa, pb = pre()
+    e1.record()
+    torch.cuda.synchronize()
+    pre_ms = e0.elapsed_time(e1) / 20
+    cfg = rp.Config.from_schedule(W, H, wk.schedule, bit_depth=12, float_frames=True, max_batch=1)
+    eng = rp.Engine(cfg)
+    for _ in range(3):
+        eng.process_pair(pa, pb)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        eng.process_pair(pa, pb)
+    e1.record()
+    torch.cuda.synchronize()
+    path_ms = e0.elapsed_time(e1) / 20
+    eng.close()
+    print(json.dumps({"mode": "preprocess", "workload": WORKLOAD, "preprocess_ms_per_pair": pre_ms,
+                      "path_ms_per_pair_float_frames": path_ms, "data": "synthetic"}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------ size sweep --
 
 SWEEP_SIZES = [(512, 512), (768, 640), (1024, 1024), (1600, 1200), (2048, 2048), (3840, 2160), (4096, 4096),
@@ -486,6 +534,8 @@ def main():
         return run_adjoint(args)
     if args.mode == "sizes":
         return run_sizes(args)
+    if args.mode == "preprocess":
+        return run_preprocess(args)
     if args.mode == "serve":
         import numpy as np  # noqa: F811
         globals()["np"] = np

@@ -63,7 +63,7 @@ typedef enum {
     RPIV_ERR_NO_DEVICE = 7    /* no usable CUDA device                           */
 } rpiv_status;
 
-typedef enum { RPIV_U8 = 1, RPIV_U16 = 2 } rpiv_pixfmt;
+typedef enum { RPIV_U8 = 1, RPIV_U16 = 2, RPIV_F32 = 3 } rpiv_pixfmt;
 
 /* Arithmetic of the correlation plane.  The argmax is taken on this plane;
  * the 5-point stencil for the Gaussian fit is always recomputed in FP32.  */
@@ -75,7 +75,7 @@ typedef enum { RPIV_DEFORM_B = 0, RPIV_DEFORM_CENTRAL = 1 } rpiv_deform;
 
 typedef struct {
     int width, height;          /* image size, px                                  */
-    rpiv_pixfmt fmt;            /* RPIV_U8 or RPIV_U16                              */
+    rpiv_pixfmt fmt;            /* RPIV_U8, RPIV_U16, or RPIV_F32 (pre-processed)  */
     int bit_depth;              /* 8, 12 or 16 (informational; no rescaling)        */
     int n_passes;               /* full-resolution passes, 1..RPIV_MAX_PASSES       */
     int window[RPIV_MAX_PASSES];     /* even, 8..128, in pass order                 */
@@ -268,6 +268,33 @@ rpiv_status rpiv_stage_vorticity(const float *u, const float *v, int nx, int ny,
  * without padding.                                                          */
 rpiv_status rpiv_stage_downsample(const void *img, size_t pitch_bytes, int fmt, int width, int height,
                                   float *out, void *cuda_stream);
+
+/* Pre-processing before the flow estimate (paper Sec. 2): a high-pass filter
+ * against the static background, then contrast-limited adaptive histogram
+ * equalisation (Zuiderveld 1994).  The paper gives no parameters; this build
+ * reads them as:
+ *   high-pass  d = max(0, n I - S), S the clamp-to-edge sum of I over the
+ *              (2 hp_radius + 1)^2 box, n its pixel count (hp_radius = 0:
+ *              d = I, n = 1); the filtered value is d / n
+ *   CLAHE      256 bins over [0, vmax + 1): bin = floor(256 d / (n (vmax+1)));
+ *              tiles_x x tiles_y tiles of ceil(W/tiles_x) x ceil(H/tiles_y)
+ *              pixels; per tile of N pixels the histogram is clipped at
+ *              max(1, floor(clip_percent N / 25600)), the excess E spread as
+ *              E / 256 to every bin plus one to the first E mod 256 bins;
+ *              map = cumulative count * vmax / N; each pixel blends the maps
+ *              of the four tiles whose centres surround it, bilinearly;
+ *              clip_percent = 0 skips the equalisation.
+ *   img        device, fmt RPIV_U8 or RPIV_U16, rows pitch_bytes apart.
+ *   out        device float32, width x height, rows `width` floats apart.
+ *   scratch    device, at least rpiv_stage_preprocess_scratch_bytes.
+ * The result, in [0, vmax], can be handed to an engine created with
+ * fmt RPIV_F32.  Errors: INVALID_ARG (nulls, sizes, hp_radius > 64, tiles
+ * outside [1, 64] or larger than the image, vmax outside [1, 65535], small
+ * scratch), CUDA.                                                           */
+rpiv_status rpiv_stage_preprocess_scratch_bytes(int width, int height, int tiles_x, int tiles_y, size_t *bytes);
+rpiv_status rpiv_stage_preprocess(const void *img, size_t pitch_bytes, int fmt, int width, int height, int vmax,
+                                  int hp_radius, int tiles_x, int tiles_y, int clip_percent, float *out,
+                                  void *scratch, size_t scratch_bytes, void *cuda_stream);
 
 /* Exponential smoothing in time (paper Sec. 2: the optical-flow estimate is
  * smoothed with a constant alpha_1 before it predicts, and the sub-pixel

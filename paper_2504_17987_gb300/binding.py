@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librpiv.so")
 
-RPIV_U8, RPIV_U16 = 1, 2
+RPIV_U8, RPIV_U16, RPIV_F32 = 1, 2, 3
 RPIV_FP32, RPIV_BF16, RPIV_FP16 = 0, 1, 2
 RPIV_DEFORM_B, RPIV_DEFORM_CENTRAL = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY", 7: "NO_DEVICE"}
@@ -28,6 +28,7 @@ EXPORTED = sorted(["rpiv_config_default", "rpiv_validate_config", "rpiv_create",
                    "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes",
                    "rpiv_stage_correlate_noalloc", "rpiv_stage_validate",
                    "rpiv_stage_interp", "rpiv_stage_vorticity", "rpiv_stage_downsample", "rpiv_stage_ema",
+                   "rpiv_stage_preprocess", "rpiv_stage_preprocess_scratch_bytes",
                    "rpiv_trace_enable", "rpiv_trace_read"])
 
 
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH):
     L.rpiv_stage_interp.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp]
     L.rpiv_stage_vorticity.argtypes = [vp, vp, i32, i32, i32, vp, vp]
     L.rpiv_stage_ema.argtypes = [vp, vp, sz, ctypes.c_float, i32, vp]
+    L.rpiv_stage_preprocess_scratch_bytes.argtypes = [i32, i32, i32, i32, ctypes.POINTER(sz)]
+    L.rpiv_stage_preprocess.argtypes = [vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, sz, vp]
     L.rpiv_stage_downsample.argtypes = [vp, sz, i32, i32, i32, vp, vp]
     L.rpiv_trace_enable.argtypes = [vp, i32]
     L.rpiv_trace_read.argtypes = [vp, ctypes.POINTER(TraceRecord), i32, ctypes.POINTER(i32)]
@@ -129,9 +132,12 @@ class Config:
     precision: str = "fp32"
     deform: str = "b"
     max_batch: int = 1
+    float_frames: bool = False  # frames are float32 (for example pre-processed), not u8/u16
 
     @property
     def fmt(self) -> int:
+        if self.float_frames:
+            return RPIV_F32
         return RPIV_U8 if self.bit_depth == 8 else RPIV_U16
 
     def to_c(self) -> _Config:
@@ -171,7 +177,11 @@ def validate_config(cfg: Config) -> Tuple[int, int]:
 def _img_check(t: torch.Tensor, cfg_fmt: int):
     if not t.is_cuda:
         raise ValueError("images must be CUDA tensors")
-    if t.is_floating_point() or t.element_size() != (1 if cfg_fmt == RPIV_U8 else 2):
+    if cfg_fmt == RPIV_F32:
+        ok = t.dtype == torch.float32
+    else:
+        ok = not t.is_floating_point() and t.element_size() == (1 if cfg_fmt == RPIV_U8 else 2)
+    if not ok:
         raise ValueError(f"image dtype {t.dtype} does not match the handle's pixel format")
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError("images must be 2-D with unit column stride")
@@ -371,6 +381,20 @@ def stage_vorticity(u, v, s: int, stream=None):
     o = torch.empty_like(u)
     _check(load().rpiv_stage_vorticity(_ptr(u), _ptr(v), nx, ny, s, _ptr(o), _stream(stream)))
     return o
+
+
+def stage_preprocess(img, vmax: int, hp: int = 7, tiles=(8, 8), clip_pct: int = 200, stream=None):
+    """High-pass filter and CLAHE (Sec. 2) of a u8/u16 device image; returns a
+    float32 image in [0, vmax] (rpiv_stage_preprocess)."""
+    H, W = img.shape
+    nbytes = ctypes.c_size_t()
+    _check(load().rpiv_stage_preprocess_scratch_bytes(W, H, int(tiles[0]), int(tiles[1]), ctypes.byref(nbytes)))
+    scratch = torch.empty(nbytes.value, dtype=torch.uint8, device=img.device)
+    out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _check(load().rpiv_stage_preprocess(_ptr(img), img.stride(0) * img.element_size(), _fmt_code(img), W, H,
+                                        int(vmax), int(hp), int(tiles[0]), int(tiles[1]), int(clip_pct), _ptr(out),
+                                        _ptr(scratch), nbytes.value, _stream(stream)))
+    return out
 
 
 def stage_ema(x, state, alpha: float, init: bool = False, stream=None):

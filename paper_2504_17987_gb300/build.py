@@ -16,7 +16,7 @@ BUILD = os.path.join(os.path.dirname(HERE), "_build", "rpiv")
 LIB = os.path.join(HERE, "librpiv.so")
 
 SOURCES = ["k_pass_fp32.cu", "k_pass_bf16.cu", "k_pass_fp16.cu", "k_deform.cu", "k_grid.cu", "k_adjoint.cu",
-           "k_static_scratch.cu", "pass_plan.cpp", "capi.cpp"]
+           "k_static_scratch.cu", "k_pre.cu", "pass_plan.cpp", "capi.cpp"]
 HEADERS = ["rpiv_internal.h", "pass_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,

@@ -80,7 +80,7 @@ struct StageDef {
 std::string check_config(const rpiv_config *c, std::vector<StageDef> *stages_out)
 {
     if (!c) return "config is NULL";
-    if (c->fmt != RPIV_U8 && c->fmt != RPIV_U16) return "fmt must be RPIV_U8 or RPIV_U16";
+    if (c->fmt != RPIV_U8 && c->fmt != RPIV_U16 && c->fmt != RPIV_F32) return "fmt must be RPIV_U8, RPIV_U16 or RPIV_F32";
     if (c->bit_depth != 8 && c->bit_depth != 12 && c->bit_depth != 16) return "bit_depth must be 8, 12 or 16";
     if (c->fmt == RPIV_U8 && c->bit_depth != 8) return "RPIV_U8 requires bit_depth 8";
     if (c->n_passes < 1 || c->n_passes > RPIV_MAX_PASSES) return "n_passes must be in [1, 4]";
@@ -274,7 +274,7 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
     const long long ios = sizeof(PairIO);
     auto ws = [&](size_t off) { return ptr_direct(h->ws + off, ps); };
     auto tab = [&](const void *field) { return ptr_table(field, ios); };
-    const int user_fmt = c.fmt == RPIV_U8 ? PIX_U8 : PIX_U16;
+    const int user_fmt = c.fmt == RPIV_U8 ? PIX_U8 : (c.fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
     const StageDef &p0 = h->stages[L];
     const bool run_pyr = L > 0 && any_nopred;
     const bool central = c.deform_mode == RPIV_DEFORM_CENTRAL;
@@ -748,7 +748,7 @@ rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, 
         return fail(RPIV_ERR_INVALID_ARG, "n = " + std::to_string(n) + " outside [1, max_batch = " +
                                               std::to_string(h->cfg.max_batch) + "]");
     if (!img_a || !img_b || !u || !v) return fail(RPIV_ERR_INVALID_ARG, "img_a, img_b, u and v must be non-NULL");
-    const size_t bpp = h->cfg.fmt == RPIV_U8 ? 1 : 2;
+    const size_t bpp = h->cfg.fmt == RPIV_U8 ? 1 : (h->cfg.fmt == RPIV_U16 ? 2 : 4);
     if (pitch_bytes < (size_t)h->cfg.width * bpp || pitch_bytes % bpp)
         return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes smaller than width * bytes per pixel or misaligned");
     if ((pred_u == nullptr) != (pred_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "pred_u and pred_v: both or neither");
@@ -839,7 +839,7 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
 {
     if (!h || !img_a || !img_b || !u || !v) return fail(RPIV_ERR_INVALID_ARG, "null argument");
     if ((grad_u == nullptr) != (grad_v == nullptr)) return fail(RPIV_ERR_INVALID_ARG, "grad_u and grad_v: both or neither");
-    const size_t bpp = h->cfg.fmt == RPIV_U8 ? 1 : 2;
+    const size_t bpp = h->cfg.fmt == RPIV_U8 ? 1 : (h->cfg.fmt == RPIV_U16 ? 2 : 4);
     if (pitch_bytes < (size_t)h->cfg.width * bpp || pitch_bytes % bpp)
         return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes smaller than width * bytes per pixel or misaligned");
     DeviceGuard dg(h->device);
@@ -865,7 +865,7 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
     std::memset(&a, 0, sizeof(a));
     a.W = d.W;
     a.H = d.H;
-    a.fmt = h->cfg.fmt == RPIV_U8 ? PIX_U8 : PIX_U16;
+    a.fmt = h->cfg.fmt == RPIV_U8 ? PIX_U8 : (h->cfg.fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
     a.pitch = (long long)pitch_bytes;
     a.img_a = ptr_direct(img_a, 0);
     a.img_b = ptr_direct(img_b, 0);
@@ -1068,6 +1068,49 @@ rpiv_status rpiv_stage_vorticity(const float *u, const float *v, int nx, int ny,
     a.ny = ny;
     a.s = step;
     CK(launch_vort(a, 1, static_cast<cudaStream_t>(cuda_stream)), "vorticity launch");
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_stage_preprocess_scratch_bytes(int width, int height, int tiles_x, int tiles_y, size_t *bytes)
+{
+    if (!bytes || width < 1 || height < 1 || width > 65536 || height > 65536 || tiles_x < 1 || tiles_y < 1 ||
+        tiles_x > 64 || tiles_y > 64)
+        return fail(RPIV_ERR_INVALID_ARG, "bad argument");
+    *bytes = preprocess_scratch_bytes(width, height, tiles_x, tiles_y);
+    return RPIV_OK;
+}
+
+rpiv_status rpiv_stage_preprocess(const void *img, size_t pitch_bytes, int fmt, int width, int height, int vmax,
+                                  int hp_radius, int tiles_x, int tiles_y, int clip_percent, float *out,
+                                  void *scratch, size_t scratch_bytes, void *cuda_stream)
+{
+    if (!img || !out || !scratch) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if (fmt != RPIV_U8 && fmt != RPIV_U16) return fail(RPIV_ERR_INVALID_ARG, "fmt must be RPIV_U8 or RPIV_U16");
+    if (width < 1 || height < 1 || width > 65536 || height > 65536) return fail(RPIV_ERR_INVALID_ARG, "image size");
+    const size_t bpp = fmt == RPIV_U8 ? 1 : 2;
+    if (pitch_bytes < (size_t)width * bpp || pitch_bytes % bpp) return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes");
+    if (vmax < 1 || vmax > 65535) return fail(RPIV_ERR_INVALID_ARG, "vmax must be in [1, 65535]");
+    if (hp_radius < 0 || hp_radius > 64) return fail(RPIV_ERR_INVALID_ARG, "hp_radius must be in [0, 64]");
+    if (tiles_x < 1 || tiles_y < 1 || tiles_x > 64 || tiles_y > 64 || tiles_x > width || tiles_y > height)
+        return fail(RPIV_ERR_INVALID_ARG, "tiles must be in [1, 64] and no more than the image size");
+    if (clip_percent < 0) return fail(RPIV_ERR_INVALID_ARG, "clip_percent must be >= 0");
+    if (scratch_bytes < preprocess_scratch_bytes(width, height, tiles_x, tiles_y))
+        return fail(RPIV_ERR_INVALID_ARG, "scratch smaller than rpiv_stage_preprocess_scratch_bytes");
+    PreArgs a;
+    a.img = img;
+    a.fmt = fmt == RPIV_U8 ? PIX_U8 : PIX_U16;
+    a.pitch = (long long)pitch_bytes;
+    a.W = width;
+    a.H = height;
+    a.vmax = vmax;
+    a.hp = hp_radius;
+    a.n = hp_radius > 0 ? (2 * hp_radius + 1) * (2 * hp_radius + 1) : 1;
+    a.tx = tiles_x;
+    a.ty = tiles_y;
+    a.clip_pct = clip_percent;
+    a.out = out;
+    a.out_pitch = width;
+    CK(launch_preprocess(a, scratch, static_cast<cudaStream_t>(cuda_stream)), "pre-processing launch");
     return RPIV_OK;
 }
 

@@ -179,6 +179,20 @@ struct VortArgs {
 };
 cudaError_t launch_vort(const VortArgs &a, int n_pairs, cudaStream_t st);
 
+// High-pass and CLAHE pre-processing of one u8/u16 image into float.
+struct PreArgs {
+    const void *img;
+    int fmt;              // PIX_U8 or PIX_U16
+    long long pitch;      // bytes
+    int W, H, vmax;
+    int hp, n;            // box radius and its pixel count (hp = 0: n = 1)
+    int tx, ty, clip_pct; // tiles; clip_pct <= 0: no equalisation
+    float *out;
+    long long out_pitch;  // floats
+};
+size_t preprocess_scratch_bytes(int W, int H, int tx, int ty);
+cudaError_t launch_preprocess(const PreArgs &a, void *scratch, cudaStream_t st);
+
 // state = init ? x : alpha x + (1 - alpha) state, elementwise over n floats.
 cudaError_t launch_ema(const float *x, float *state, size_t n, float alpha, int init, cudaStream_t st);
 
