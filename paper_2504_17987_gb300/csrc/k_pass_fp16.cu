@@ -7,7 +7,7 @@ namespace rpiv {
 template <int RC>
 static cudaError_t go_fp16(const PassArgs &a, dim3 grid, int smem, cudaStream_t st)
 {
-    pass_kernel<RC, PREC_FP16><<<grid, PASS_THREADS, smem, st>>>(a);
+    pass_kernel<RC, PREC_FP16, 0><<<grid, PASS_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -32,11 +32,11 @@ void prepare_pass_fp16()
     auto set_smem = [](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     };
-    set_smem(pass_kernel<1, PREC_FP16>);
-    set_smem(pass_kernel<2, PREC_FP16>);
-    set_smem(pass_kernel<4, PREC_FP16>);
-    set_smem(pass_kernel<6, PREC_FP16>);
-    set_smem(pass_kernel<8, PREC_FP16>);
+    set_smem(pass_kernel<1, PREC_FP16, 0>);
+    set_smem(pass_kernel<2, PREC_FP16, 0>);
+    set_smem(pass_kernel<4, PREC_FP16, 0>);
+    set_smem(pass_kernel<6, PREC_FP16, 0>);
+    set_smem(pass_kernel<8, PREC_FP16, 0>);
     cudaGetLastError();
 }
 

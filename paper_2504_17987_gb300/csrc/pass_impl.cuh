@@ -78,6 +78,7 @@ __device__ __forceinline__ uint16_t to_h16(float x)
 
 struct TileGeom {
     int R, ND, NP;
+    int w, s, G, kb;  // window, step, block size, blocks per window side (compile-time when specialised)
     int wx0, wy0, nwx, nwy, nwin;
     int aw, ah, ax0, ay0;
     int BC, BR, OFFB;
@@ -130,7 +131,7 @@ __device__ __forceinline__ int up4(int x) { return (x + 3) & ~3; }
 // a multiple of 4 every row is one 16-byte-aligned bulk copy completing on an
 // mbarrier (bounded wait: on timeout the error word is set and false returned);
 // otherwise plain loads.
-static __device__ bool load_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs,
+static __device__ __forceinline__ bool load_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs,
                                     uint64_t *bar)
 {
     const PassPlan &P = a.plan;
@@ -140,7 +141,7 @@ static __device__ bool load_regions(const PassArgs &a, const TileGeom &g, int pa
     const long long dp = a.def_pitch;
     const int M = a.def_margin;
     const float *a0 = asrc + (long long)(g.ay0 + M) * dp + (g.ax0 + M);
-    if (a.s % 4 == 0) {
+    if (g.s % 4 == 0) {
         // B' rows start at smem column 0, i.e. global column ax0 + M - padl
         const float *b0 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 + M - P.padl);
         const int acols = up4(g.aw), bcols = up4(g.OFFB + g.BC);
@@ -178,7 +179,7 @@ static __device__ bool load_regions(const PassArgs &a, const TileGeom &g, int pa
 // one column left so that every column pair starts 4-byte aligned), with zeros
 // wherever fragments may reach outside the staged region.
 template <int PREC>
-__device__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, uint16_t *TA,
+__device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, uint16_t *TA,
                           uint16_t *TB)
 {
     const PassPlan &P = a.plan;
@@ -204,10 +205,10 @@ __device__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As,
 //   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]         (threads along r, odd pitch)
 // so V[r][c] is the sum over the w x w box whose top-left logical B' pixel
 // is (r, c).  Each thread restarts its running sum every 8 outputs.
-static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
+static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
 {
     const PassPlan &P = a.plan;
-    const int w = a.w, tid = threadIdx.x;
+    const int w = g.w, tid = threadIdx.x;
     const int cp = P.h_pitch;  // pitch of C and V (odd)
     float *C1 = Cs, *C2 = Cs + g.vh * cp;
     const int nsegv = (g.vh + 7) / 8;
@@ -257,11 +258,11 @@ static __device__ void box_sums(const PassArgs &a, const TileGeom &g, const floa
 
 // Sum and centred sum of squares of every G x G block of A (two passes; one
 // warp per block, lanes along the rows): bst[b] = (sum, M2).
-static __device__ void block_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
+static __device__ __forceinline__ void block_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int G = P.G;
+    const int G = g.G;
     const float n = (float)(G * G);
     for (int b = warp; b < g.nb; b += nwarps) {
         const int bxi = b % g.nbx, byi = b / g.nbx;
@@ -282,14 +283,14 @@ static __device__ void block_stats(const PassArgs &a, const TileGeom &g, const f
 
 // Window mean and energy from its blocks (parallel-variance identity):
 // E = sum M2_b + n_b sum (mean_b - mean)^2, in a fixed order.
-static __device__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *bst, float *stats)
+static __device__ __forceinline__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *bst, float *stats)
 {
     const PassPlan &P = a.plan;
-    const int G = P.G, kb = a.w / G;
-    const float nb = (float)(G * G), n = (float)(a.w * a.w);
+    const int G = g.G, kb = g.w / G;
+    const float nb = (float)(G * G), n = (float)(g.w * g.w);
     for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
         const int wxi = wi % g.nwx, wyi = wi / g.nwx;
-        const int bx0 = (wxi * a.s) / G, by0 = (wyi * a.s) / G;
+        const int bx0 = (wxi * g.s) / G, by0 = (wyi * g.s) / G;
         float s = 0.f;
         for (int yy = 0; yy < kb; ++yy)
             for (int xx = 0; xx < kb; ++xx) s += bst[(by0 + yy) * g.nbx + bx0 + xx].x;
@@ -312,14 +313,14 @@ static __device__ void window_stats(const PassArgs &a, const TileGeom &g, const 
 // the 2R+1 accumulators of its sx row in registers; rows are streamed from
 // shared memory four columns at a time with aligned 128-bit loads.
 template <int R>
-__device__ void block_planes_fp32(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, float *Ps)
+__device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, float *Ps)
 {
     constexpr int ND = 2 * R + 1;
     constexpr int NP = ND * ND;
     constexpr int MIS = ((-R) % 4 + 4) % 4;
     constexpr int NQ = (4 + 2 * R + MIS + 3) / 4;
     const PassPlan &P = a.plan;
-    const int G = P.G, RG = P.RGx, rows = G / RG;
+    const int G = g.G, RG = P.RGx, rows = G / RG;
     const int items = g.nb * ND * RG;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int syi = it % ND;
@@ -360,12 +361,12 @@ __device__ void block_planes_fp32(const PassArgs &a, const TileGeom &g, const fl
 }
 
 // Runtime radius (any R up to RPIV_MAX_RADIUS): scalar loads, sx in chunks of 8.
-static __device__ void block_planes_fp32_generic(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs,
+static __device__ __forceinline__ void block_planes_fp32_generic(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs,
                                           float *Ps)
 {
     const PassPlan &P = a.plan;
     const int R = g.R, ND = g.ND, NP = g.NP;
-    const int G = P.G, RG = P.RGx, rows = G / RG;
+    const int G = g.G, RG = P.RGx, rows = G / RG;
     const int nch = (ND + 7) / 8;
     const int items = g.nb * ND * RG * nch;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -446,7 +447,7 @@ __device__ __forceinline__ uint32_t ld_pair(const uint16_t *p) { return *reinter
 // directly, for every shift, across the rows (A rows outside the group enter
 // as zeros).  16 x 8 tiles: MT tiles of sx, NT tiles of sy.
 template <int R, int PREC>
-__device__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint16_t *TA, const uint16_t *TB,
+__device__ __forceinline__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint16_t *TA, const uint16_t *TB,
                                 float *Ps)
 {
     constexpr int ND = 2 * R + 1;
@@ -456,7 +457,7 @@ __device__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
-    const int G = P.G, RG = P.RGx, rows = G / RG;
+    const int G = g.G, RG = P.RGx, rows = G / RG;
     const uint16_t *TB1 = TB + P.tb_rows * P.tcb_pitch;
     // smem column of Toeplitz element (m, k) of m-tile mt at block column X:
     //     padl - R + X + 16 mt + m + k;  X is even, so its parity is that of padl - R + m
@@ -589,23 +590,23 @@ struct WinShared {
 // (ties keep the smallest row-major index), plane values of the stencil.
 // RC >= 0: compile-time radius (shift decoding without integer division).
 template <int RC>
-static __device__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
+static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
                                       const float *stats, bool tc, const WinShared &ws)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int R = RC >= 0 ? RC : g.R;
     const int ND = 2 * R + 1, NP = ND * ND;
-    const int G = P.G, kb = a.w / G, RG = P.RGx;
-    const float inv_n = 1.f / (float)(a.w * a.w), tau = TAU_PER_PIXEL * (float)(a.w * a.w);
+    const int G = g.G, kb = g.w / G, RG = P.RGx;
+    const float inv_n = 1.f / (float)(g.w * g.w), tau = TAU_PER_PIXEL * (float)(g.w * g.w);
     const int cp = P.v_pitch;
     const float *V1 = Vs, *V2 = Vs + g.vh * cp;
     for (int wi = warp; wi < g.nwin; wi += nwarps) {
         const int wxi = wi % g.nwx, wyi = wi / g.nwx;
         const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
-        const int bx0 = (wxi * a.s) / G, by0 = (wyi * a.s) / G;
-        const float *v1 = V1 + (wyi * a.s + R + 1) * cp + wxi * a.s + R + 1;
-        const float *v2 = V2 + (wyi * a.s + R + 1) * cp + wxi * a.s + R + 1;
+        const int bx0 = (wxi * g.s) / G, by0 = (wyi * g.s) / G;
+        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float *v2 = V2 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
         // the window's partial planes: for each of its kb block rows, kb * RG
         // consecutive planes of NP floats
         const float *prow = Ps + (size_t)(by0 * g.nbx + bx0) * RG * NP;
@@ -661,12 +662,12 @@ static __device__ void plane_and_peak(const PassArgs &a, const TileGeom &g, cons
 
 // Direct FP32 numerators of the stencil points the plane cannot supply: one
 // warp per (window, 8-row group), lanes along the columns, five accumulators.
-static __device__ void stencil_direct(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs,
+static __device__ __forceinline__ void stencil_direct(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs,
                                       const WinShared &ws)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int w = a.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
+    const int w = g.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
     for (int it = warp; it < g.nwin * ngr; it += nwarps) {
         const int wi = it / ngr, gr = it - wi * ngr;
         const int need = ws.need[wi];
@@ -675,9 +676,9 @@ static __device__ void stencil_direct(const PassArgs &a, const TileGeom &g, cons
         const int ky = q / ND - R, kx = q % ND - R;
         const int wxi = wi % g.nwx, wyi = wi / g.nwx;
         const int rows = min(8, w - 8 * gr);
-        const float *abase = As + (wyi * a.s + 8 * gr) * P.a_pitch + wxi * a.s;
+        const float *abase = As + (wyi * g.s + 8 * gr) * P.a_pitch + wxi * g.s;
         // B' at A pixel (r, x) and shift (sy, sx): row r + sy + R + 1, column x + sx + padl
-        const float *bbase = Bs + (wyi * a.s + 8 * gr + ky + R + 1) * P.b_pitch + P.padl + wxi * a.s + kx;
+        const float *bbase = Bs + (wyi * g.s + 8 * gr + ky + R + 1) * P.b_pitch + P.padl + wxi * g.s + kx;
         float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         for (Walk2D e(lane, 32, w); e.y < rows; e.next()) {
             const float av = abase[e.y * P.a_pitch + e.x];
@@ -701,11 +702,11 @@ static __device__ void stencil_direct(const PassArgs &a, const TileGeom &g, cons
 }
 
 // Stencil values, Gaussian fit and outputs (one thread per window).
-static __device__ void finalize(const PassArgs &a, const TileGeom &g, const float *Vs, const float *stats,
+static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeom &g, const float *Vs, const float *stats,
                                 const WinShared &ws, int pair)
 {
     const PassPlan &P = a.plan;
-    const int w = a.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
+    const int w = g.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
     const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
     const int cp = P.v_pitch;
     const float *V1 = Vs, *V2 = Vs + g.vh * cp;
@@ -735,7 +736,7 @@ static __device__ void finalize(const PassArgs &a, const TileGeom &g, const floa
                 stencil_shift(p, ky, kx, sy, sx);
                 float num = 0.f;
                 for (int gr = 0; gr < ngr; ++gr) num += ws.dpart[(wi * ngr + gr) * 5 + p];
-                const int vo = (wyi * a.s + R + 1 + sy) * cp + wxi * a.s + R + 1 + sx;
+                const int vo = (wyi * g.s + R + 1 + sy) * cp + wxi * g.s + R + 1 + sx;
                 c5[p] = zncc_from(num, muA, EA, V1[vo], V2[vo], inv_n, tau);
             } else {
                 c5[p] = ws.c5[wi * 5 + p];
@@ -752,7 +753,7 @@ static __device__ void finalize(const PassArgs &a, const TileGeom &g, const floa
 // A tile whose region load did not complete: its windows are reported
 // invalid (the predictor passes through, info 0), as for a degenerate window,
 // so that the outlier test replaces them; the error word carries the event.
-static __device__ void invalid_tile(const PassArgs &a, const TileGeom &g, int pair)
+static __device__ __forceinline__ void invalid_tile(const PassArgs &a, const TileGeom &g, int pair)
 {
     const float *pu = (const float *)resolve(a.pred_u, pair);
     const float *pv = (const float *)resolve(a.pred_v, pair);
@@ -769,8 +770,10 @@ static __device__ void invalid_tile(const PassArgs &a, const TileGeom &g, int pa
 
 // ------------------------------------------------------------- the kernel --
 
-template <int RC, int PREC>
-__global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
+// GC > 0: a kernel specialised for blocks of GC pixels, windows of 2 GC and
+// steps of GC (50 % overlap), so that window, step and block loops unroll.
+template <int RC, int PREC, int GC>
+__global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 && RC <= 4)) ? 5 : 3) pass_kernel(const PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const PassPlan &P = a.plan;
@@ -778,8 +781,12 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
     g.R = RC >= 0 ? RC : a.R;
     g.ND = 2 * g.R + 1;
     g.NP = g.ND * g.ND;
+    g.G = GC > 0 ? GC : P.G;
+    g.w = GC > 0 ? 2 * GC : a.w;
+    g.s = GC > 0 ? GC : a.s;
+    g.kb = g.w / g.G;
     const int pair = blockIdx.z;
-    const int s = a.s, w = a.w;
+    const int s = g.s, w = g.w;
     g.wx0 = blockIdx.x * P.TX;
     g.wy0 = blockIdx.y * P.TY;
     g.nwx = min(P.TX, a.nx - g.wx0);
@@ -794,8 +801,8 @@ __global__ void __launch_bounds__(PASS_THREADS) pass_kernel(const PassArgs a)
     g.OFFB = P.padl - (g.R + 1);
     g.hw = g.BC - w + 1;
     g.vh = g.BR - w + 1;
-    g.nbx = g.aw / P.G;
-    g.nby = g.ah / P.G;
+    g.nbx = g.aw / g.G;
+    g.nby = g.ah / g.G;
     g.nb = g.nbx * g.nby;
 
     float *As = reinterpret_cast<float *>(smem + P.off_a);

@@ -211,13 +211,15 @@ int min_ctas(int w, int prec)
 
 // Tiles: among shapes of up to 8 x 8 windows (not necessarily square) that
 // leave room for min_ctas() CTAs per SM, counting shared memory (228 KB per
-// SM, 1 KB reserved per CTA), threads and registers (48 per thread; 64 for
-// the FP32 and 80 for the tensor-core kernel at r = 8), the one with the most
+// SM, 1 KB reserved per CTA), threads and registers, the one with the most
 // windows; ties go to fewer blocks per window, then to the squarer tile.  If
 // none fits, the shape with the most CTAs per SM.
 bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
 {
-    const int regs = R >= 8 ? (prec == PREC_FP32 ? 64 : 80) : 48;
+    // registers per thread as the kernels are built: the FP32 kernel is bounded
+    // to five CTAs per SM up to r = 4 (48 registers), three beyond; the
+    // tensor-core kernel to three
+    const int regs = (prec == PREC_FP32 ? R <= 4 : R <= 6) ? 48 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     const int override_kb = smem_budget_override();
     const int target = min_ctas(w, prec);
