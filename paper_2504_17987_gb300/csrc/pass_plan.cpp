@@ -219,7 +219,7 @@ bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan 
     // registers per thread as the kernels are built: the FP32 kernel is bounded
     // to five CTAs per SM up to r = 4 (48 registers), three beyond; the
     // tensor-core kernel to three
-    const int regs = (prec == PREC_FP32 ? R <= 4 : R <= 6) ? 48 : 80;
+    const int regs = (prec == PREC_FP32 && R <= 4) ? 48 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     const int override_kb = smem_budget_override();
     const int target = min_ctas(w, prec);
