@@ -39,12 +39,6 @@ __device__ __forceinline__ void axis_weight(int pos, int n, float c0, int s, int
     t = f - (float)ia;
 }
 
-template <typename T>
-__device__ __forceinline__ float tap(const unsigned char *row, int x)
-{
-    return (float)__ldg(reinterpret_cast<const T *>(row) + x);
-}
-
 constexpr int NROW_CAP = DTY / 3 + 4;  // node rows a tile touches (steps >= 3, checked on the host)
 
 __device__ __forceinline__ float warp_min(float v)
@@ -58,6 +52,63 @@ __device__ __forceinline__ float warp_max(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// The tile in slices of 32 rows; within a slice all rows of a thread are
+// unrolled so that their gathers are in flight together; rows and columns
+// past the grown image are computed on clamped coordinates and not stored.
+// Off: the integer type of pixel offsets.
+template <typename T, typename Off>
+__device__ __forceinline__ void deform_rows(const DeformArgs &a, const unsigned char *img, float *out, bool has,
+                                            bool inside, int dj, Off pe, int x, int y0, int lx, int ly0,
+                                            const float (*cu)[DTX], const float (*cv)[DTX], const int *riy,
+                                            const float *rty)
+{
+    const T *base = reinterpret_cast<const T *>(img);
+    for (int half = 0; half < DTY / 32; ++half) {
+        float res[DROWS];
+#pragma unroll
+        for (int k = 0; k < DROWS; ++k) {
+            const int ly = 32 * half + ly0 + 4 * k, y = y0 + ly;
+            float du = 0.f, dv = 0.f;
+            if (has) {
+                const int j0 = riy[ly];
+                const float ty = rty[ly];
+                const float u0 = cu[j0][lx], u1 = cu[j0 + dj][lx];
+                const float v0 = cv[j0][lx], v1 = cv[j0 + dj][lx];
+                du = a.scale * (u0 + ty * (u1 - u0));
+                dv = a.scale * (v0 + ty * (v1 - v0));
+                if (!inside) {
+                    // NaN or absurd predictor values are clamped so the index math cannot overflow
+                    du = fminf(fmaxf(du, -1048576.f), 1048576.f);
+                    dv = fminf(fmaxf(dv, -1048576.f), 1048576.f);
+                }
+            }
+            const float fx = floorf(du), fy = floorf(dv);
+            const float tx = du - fx, ty = dv - fy;
+            int xa = x + (int)fx, ya = y + (int)fy;
+            int xb = xa + 1, yb = ya + 1;
+            if (!inside) {
+                xb = min(max(xb, 0), a.W - 1);
+                yb = min(max(yb, 0), a.H - 1);
+                xa = min(max(xa, 0), a.W - 1);
+                ya = min(max(ya, 0), a.H - 1);
+            }
+            const T *rowa = base + (Off)ya * pe, *rowb = base + (Off)yb * pe;
+            const float b00 = (float)__ldg(rowa + xa), b10 = (float)__ldg(rowa + xb);
+            const float b01 = (float)__ldg(rowb + xa), b11 = (float)__ldg(rowb + xb);
+            const float top = b00 + tx * (b10 - b00), bot = b01 + tx * (b11 - b01);
+            res[k] = top + ty * (bot - top);
+        }
+        if (x < a.W + a.M) {
+            float *o = out + (long long)(y0 + 32 * half + ly0 + a.M) * a.out_pitch + (x + a.M);
+#pragma unroll
+            for (int k = 0; k < DROWS; ++k) {
+                const int y = y0 + 32 * half + ly0 + 4 * k;
+                if (y < a.H + a.M) o[(long long)(4 * k) * a.out_pitch] = res[k];
+            }
+        }
+    }
 }
 
 // The field is bilinear in the nodes: the tile first interpolates every node
@@ -159,50 +210,12 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
                         x0 + DTX - 1 + floorf(umax) + 2.f <= (float)(a.W - 1) && y0 + floorf(vmin) - 1.f >= 0.f &&
                         y0 + DTY - 1 + floorf(vmax) + 2.f <= (float)(a.H - 1);
     const int dj = a.ny > 1 ? 1 : 0;
-    // the tile in slices of 32 rows; within a slice all rows of a thread are
-    // unrolled so that their gathers are in flight together; rows and columns
-    // past the grown image are computed on clamped coordinates and not stored
-    for (int half = 0; half < DTY / 32; ++half) {
-    float res[DROWS];
-#pragma unroll
-    for (int k = 0; k < DROWS; ++k) {
-        const int ly = 32 * half + ly0 + 4 * k, y = y0 + ly;
-        float du = 0.f, dv = 0.f;
-        if (has) {
-            const int j0 = riy[ly];
-            const float ty = rty[ly];
-            const float u0 = cu[j0][lx], u1 = cu[j0 + dj][lx];
-            const float v0 = cv[j0][lx], v1 = cv[j0 + dj][lx];
-            du = a.scale * (u0 + ty * (u1 - u0));
-            dv = a.scale * (v0 + ty * (v1 - v0));
-            // NaN or absurd predictor values are clamped so the index math cannot overflow
-            du = fminf(fmaxf(du, -1048576.f), 1048576.f);
-            dv = fminf(fmaxf(dv, -1048576.f), 1048576.f);
-        }
-        const float fx = floorf(du), fy = floorf(dv);
-        const float tx = du - fx, ty = dv - fy;
-        int xa = x + (int)fx, ya = y + (int)fy;
-        int xb = xa + 1, yb = ya + 1;
-        if (!inside) {
-            xb = min(max(xb, 0), a.W - 1);
-            yb = min(max(yb, 0), a.H - 1);
-            xa = min(max(xa, 0), a.W - 1);
-            ya = min(max(ya, 0), a.H - 1);
-        }
-        const unsigned char *rowa = img + (long long)ya * a.pitch, *rowb = img + (long long)yb * a.pitch;
-        const float b00 = tap<T>(rowa, xa), b10 = tap<T>(rowa, xb);
-        const float b01 = tap<T>(rowb, xa), b11 = tap<T>(rowb, xb);
-        const float top = b00 + tx * (b10 - b00), bot = b01 + tx * (b11 - b01);
-        res[k] = top + ty * (bot - top);
-    }
-    if (x < a.W + a.M) {
-#pragma unroll
-        for (int k = 0; k < DROWS; ++k) {
-            const int y = y0 + 32 * half + ly0 + 4 * k;
-            if (y < a.H + a.M) out[(long long)(y + a.M) * a.out_pitch + (x + a.M)] = res[k];
-        }
-    }
-    }
+    const long long pe = a.pitch / (long long)sizeof(T);  // row pitch in pixels (a multiple of the pixel size)
+    // 32-bit pixel offsets when the whole image fits them
+    if ((long long)a.H * pe < (1LL << 31))
+        deform_rows<T, int>(a, img, out, has, inside, dj, (int)pe, x, y0, lx, ly0, cu, cv, riy, rty);
+    else
+        deform_rows<T, long long>(a, img, out, has, inside, dj, pe, x, y0, lx, ly0, cu, cv, riy, rty);
 }
 
 // one kernel per pixel type, so that each holds a single copy of the tile's
