@@ -315,3 +315,34 @@ def test_ema_stage_matches_oracle():
     assert np.array_equal(out, x)
     with pytest.raises(rp.RpivError):
         rp.stage_ema(tx, ts.clone(), 1.5)
+
+
+@pytest.mark.parametrize("w,s,R,precision", [(32, 16, 12, "fp32"), (128, 64, 4, "fp32"), (8, 4, 2, "fp32"),
+                                             (16, 8, 16, "fp32"), (96, 48, 4, "bf16"), (16, 8, 8, "bf16")])
+def test_correlate_edge_shapes(w, s, R, precision):
+    # runtime-radius kernel (r 12, 16), the largest window, the smallest, and
+    # tensor-core shapes outside the benchmark's; ragged tails on both axes
+    W, H = 8 * w + 2 * R + 11, 6 * w + 2 * R + 7
+    wk = wl.paper_1mp(W=W, H=H)
+    A, B = wk.render()
+    nx, ny = oracle.grid_n(W, w, s), oracle.grid_n(H, w, s)
+    pu, pv = smooth_field(nx, ny, w, s, seed=w + 3 * R, base=(12.0, 0.0), amp=1.0)
+    r = compare_pass(A, B, w, s, R, pu, pv, precision=precision)
+    if precision == "fp32":
+        check_fp32_pass(r, R)
+    else:
+        ref = r["ref"]
+        same = (r["ky"] == ref.peaks[..., 0]) & (r["kx"] == ref.peaks[..., 1])
+        assert same.mean() >= 0.98, f"{precision} peak agreement {same.mean():.4f}"
+        assert near_tie_ok(ref.plane, r["ky"], r["kx"], R, 0.02)[~same].all()
+        f = r["forced"]
+        assert np.maximum(np.abs(r["u"] - f.u), np.abs(r["v"] - f.v)).max() <= TOL_PX
+
+
+def test_tensor_core_path_rejects_windows_beyond_shared_memory():
+    # a 128 px window's 16-bit copies do not fit one CTA's shared memory: a clear
+    # UNSUPPORTED status, not a launch failure
+    A = np.zeros((300, 300), np.uint8)
+    with pytest.raises(rp.RpivError) as ei:
+        rp.stage_correlate(dev(A), dev(A), 128, 64, 4, None, None, precision="bf16")
+    assert ei.value.status == 2
