@@ -19,7 +19,14 @@ Scheduling (host side, one thread):
   * completions are detected by polling CUDA events; the latency of a request
     is arrival -> its results complete on the device.
 Requests that arrive while batches run are admitted as slots and memory free
-up, so work of different sizes overlaps on the device.  The kernels treat
+up, so work of different sizes overlaps on the device.
+
+While a run is live the cyclic garbage collector does not run on its own: the
+objects alive at the start are frozen out of its scans, and only the young
+generations are collected, at moments when the loop is waiting on the device.
+A full (generation-2) pass over a run's requests and tensors takes tens of
+milliseconds on one host core and would otherwise stall every request
+queued behind it.  The kernels treat
 every pair independently (the batch index only selects data), so a request's
 result does not depend on what it is batched with.
 
@@ -31,6 +38,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import heapq
 import math
 import time
@@ -231,31 +239,50 @@ class Scheduler:
         self.in_flight = still
         return finished
 
-    def run(self, requests: Sequence[Request], realtime: bool = True, on_idle: Callable[[], None] = None) -> dict:
+    def run(self, requests: Sequence[Request], realtime: bool = True, on_idle: Callable[[], None] = None,
+            young_gc_at: int = 700) -> dict:
         """Serve all requests.  realtime: arrivals follow the wall clock;
-        otherwise every request is available at once (saturation run)."""
+        otherwise every request is available at once (saturation run).
+        young_gc_at: allocations since the last young collection after which
+        an idle loop iteration collects generations 0 and 1 (0: the
+        collector is left as it is)."""
         arrivals = sorted(requests, key=lambda r: r.arrival)
         heap = [(r.arrival, r.rid, r) for r in arrivals]
         heapq.heapify(heap)
-        self.t0 = self.clock()
-        now_fn = lambda: self.clock() - self.t0  # noqa: E731
-        total = len(arrivals)
-        while len(self.done) + len(self.dropped) < total:
-            now = now_fn()
-            while heap and (not realtime or heap[0][0] <= now):
-                _, _, r = heapq.heappop(heap)
-                if not realtime:
-                    r.arrival = min(r.arrival, now)
-                if r.stream in self.failed_streams:
-                    r.error = "stream failed"
-                    self.dropped.append(r)
-                else:
-                    self.fifo[r.stream].append(r)
-            progressed = self._complete(now_fn)
-            progressed |= self._dispatch(now_fn())
-            if not progressed and on_idle is not None:
-                on_idle()
-        wall = now_fn()
+        pause_gc = young_gc_at > 0
+        was_enabled = gc.isenabled()
+        if pause_gc:
+            gc.collect()
+            gc.freeze()
+            gc.disable()
+        try:
+            self.t0 = self.clock()
+            now_fn = lambda: self.clock() - self.t0  # noqa: E731
+            total = len(arrivals)
+            while len(self.done) + len(self.dropped) < total:
+                now = now_fn()
+                while heap and (not realtime or heap[0][0] <= now):
+                    _, _, r = heapq.heappop(heap)
+                    if not realtime:
+                        r.arrival = min(r.arrival, now)
+                    if r.stream in self.failed_streams:
+                        r.error = "stream failed"
+                        self.dropped.append(r)
+                    else:
+                        self.fifo[r.stream].append(r)
+                progressed = self._complete(now_fn)
+                progressed |= self._dispatch(now_fn())
+                if not progressed:
+                    if pause_gc and gc.get_count()[0] >= young_gc_at:
+                        gc.collect(1)
+                    if on_idle is not None:
+                        on_idle()
+            wall = now_fn()
+        finally:
+            if pause_gc:
+                gc.unfreeze()
+                if was_enabled:
+                    gc.enable()
         return self.report(wall)
 
     def report(self, wall: float) -> dict:

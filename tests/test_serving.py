@@ -169,6 +169,49 @@ def test_executor_error_keeps_the_old_predictor():
     assert all(r.mode == sv.COLD for r in sch.done if r.stream == 1)
 
 
+def test_collector_paused_during_run_and_restored_after():
+    import gc
+    clock = FakeClock()
+    ex = FakeExecutor(clock)
+    reqs = make_requests(n_streams=3, frames=4)
+    sch = sv.Scheduler(ex, max_batch=4, slots=2, hbm_budget=1e9, clock=clock)
+    seen = {"enabled": set(), "young": 0}
+
+    def idle():
+        clock.t += 1e-4
+        seen["enabled"].add(gc.isenabled())
+        # garbage with reference cycles, so young collections have work
+        for _ in range(50):
+            a = []
+            a.append(a)
+        if gc.get_count()[0] < 5:
+            seen["young"] += 1
+    assert gc.isenabled()
+    rep = sch.run(reqs, on_idle=idle, young_gc_at=100)
+    assert rep["requests"] == len(reqs)
+    assert seen["enabled"] == {False}
+    assert seen["young"] > 0            # young generations were collected at idle
+    assert gc.isenabled() and gc.get_freeze_count() == 0
+
+    # young_gc_at=0 leaves the collector alone
+    seen["enabled"].clear()
+    sv.Scheduler(ex, max_batch=4, slots=2, hbm_budget=1e9, clock=clock).run(
+        make_requests(n_streams=2, frames=2), on_idle=idle, young_gc_at=0)
+    assert seen["enabled"] == {True}
+
+
+def test_collector_restored_when_the_executor_raises():
+    import gc
+
+    class Boom(FakeExecutor):
+        def submit(self, *a):
+            raise RuntimeError("device lost")
+    clock = FakeClock()
+    with pytest.raises(RuntimeError):
+        sv.Scheduler(Boom(clock), clock=clock).run(make_requests(n_streams=1, frames=1), realtime=False)
+    assert gc.isenabled() and gc.get_freeze_count() == 0
+
+
 # ------------------------------------------------------------------- GPU --
 
 @pytest.mark.gpu
