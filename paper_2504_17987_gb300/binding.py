@@ -18,6 +18,18 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librpiv.so")
 
 RPIV_U8, RPIV_U16, RPIV_F32 = 1, 2, 3
+
+
+def _poison() -> bool:
+    """RPIV_POISON_SCRATCH=1 (a test setting): scratch and outputs start as
+    0xFF bytes (NaN as float), so that a value no kernel wrote surfaces."""
+    return os.environ.get("RPIV_POISON_SCRATCH", "") == "1"
+
+
+def _fresh(t: torch.Tensor) -> torch.Tensor:
+    if _poison():
+        t.view(torch.uint8).fill_(0xFF)
+    return t
 RPIV_FP32, RPIV_BF16, RPIV_FP16 = 0, 1, 2
 RPIV_DEFORM_B, RPIV_DEFORM_CENTRAL = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY", 7: "NO_DEVICE"}
@@ -336,13 +348,13 @@ def stage_correlate(a, b, w: int, s: int, r: int, pred_u=None, pred_v=None, prec
     H, W = a.shape
     nx, ny = (W - w) // s + 1, (H - w) // s + 1
     dev = a.device
-    u = torch.empty((ny, nx), dtype=torch.float32, device=dev)
-    v = torch.empty_like(u)
-    info = torch.empty((ny, nx), dtype=torch.int32, device=dev)
+    u = _fresh(torch.empty((ny, nx), dtype=torch.float32, device=dev))
+    v = _fresh(torch.empty_like(u))
+    info = _fresh(torch.empty((ny, nx), dtype=torch.int32, device=dev))
     dm = RPIV_DEFORM_CENTRAL if deform == "central" else RPIV_DEFORM_B
     nbytes = ctypes.c_size_t()
     _check(load().rpiv_stage_correlate_scratch_bytes(W, H, r, dm, ctypes.byref(nbytes)))
-    scratch = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=dev)
+    scratch = _fresh(torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=dev))
     _check(load().rpiv_stage_correlate(_ptr(a), _ptr(b), a.stride(0) * a.element_size(), _fmt_code(a), W, H, w, s, r,
                                        PRECISIONS[precision], dm, _ptr(pred_u), _ptr(pred_v), _ptr(u), _ptr(v),
                                        _ptr(info), _ptr(scratch), nbytes.value, _stream(stream)))
@@ -389,7 +401,7 @@ def stage_preprocess(img, vmax: int, hp: int = 7, tiles=(8, 8), clip_pct: int = 
     H, W = img.shape
     nbytes = ctypes.c_size_t()
     _check(load().rpiv_stage_preprocess_scratch_bytes(W, H, int(tiles[0]), int(tiles[1]), ctypes.byref(nbytes)))
-    scratch = torch.empty(nbytes.value, dtype=torch.uint8, device=img.device)
+    scratch = _fresh(torch.empty(nbytes.value, dtype=torch.uint8, device=img.device))
     out = torch.empty((H, W), dtype=torch.float32, device=img.device)
     _check(load().rpiv_stage_preprocess(_ptr(img), img.stride(0) * img.element_size(), _fmt_code(img), W, H,
                                         int(vmax), int(hp), int(tiles[0]), int(tiles[1]), int(clip_pct), _ptr(out),

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -15,6 +16,21 @@
 
 #include "rpiv.h"
 #include "rpiv_internal.h"
+
+namespace {
+
+// RPIV_POISON_SCRATCH=1: fill freshly allocated workspaces with 0xFF bytes
+// (NaN as float) so that reads of unwritten values surface (testing aid)
+bool poison_scratch()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("RPIV_POISON_SCRATCH");
+        return e && std::strcmp(e, "1") == 0;
+    }();
+    return on;
+}
+
+}  // namespace
 
 using namespace rpiv;
 
@@ -695,6 +711,10 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
         cudaGetLastError();
         return cleanup(RPIV_ERR_OOM, "workspace allocation of " + std::to_string(h->ws_bytes) + " bytes failed");
     }
+    // RPIV_POISON_SCRATCH=1 (a test setting) fills the workspace with NaN
+    // bytes, so that any read of a value no kernel wrote shows up as NaN
+    if (poison_scratch() && cudaMemset(h->ws, 0xFF, h->ws_bytes) != cudaSuccess)
+        return cleanup(RPIV_ERR_CUDA, "workspace fill failed");
     e = cudaMalloc(&h->io_dev, sizeof(PairIO) * cfg->max_batch);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -858,6 +878,8 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
             return fail(RPIV_ERR_OOM, "adjoint workspace allocation failed");
         }
         h->adj_bytes = need;
+        if (poison_scratch() && cudaMemset(h->adj_ws, 0xFF, need) != cudaSuccess)
+            return fail(RPIV_ERR_CUDA, "adjoint workspace fill failed");
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (h->done_recorded) CK(cudaStreamWaitEvent(st, h->done_ev, 0), "ordering wait");

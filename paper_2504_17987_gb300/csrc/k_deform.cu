@@ -23,23 +23,24 @@ namespace {
 constexpr int DTX = 64, DTY = 64;  // output pixels per CTA
 constexpr int DROWS = 8;           // rows per thread and 32-row slice (256 threads = 64 columns x 4 row phases)
 constexpr int NODE_CAP = 640;      // nodes a tile can touch (checked on the host)
+constexpr int NROW_CAP = DTY / 3 + 4;  // node rows a tile touches (steps >= 3, checked on the host)
 
-__device__ __forceinline__ void axis_weight(int pos, int n, float c0, int s, int &i0, float &t)
+// cell index and weight of a pixel position along one axis of the node grid
+// (node i at c0 + i s; positions outside the hull take the border value)
+__device__ __forceinline__ void axis_weight(int pos, int n, float c0, float inv_s, int &i0, float &t)
 {
     if (n <= 1) {
         i0 = 0;
         t = 0.f;
         return;
     }
-    float f = ((float)pos - c0) / (float)s;
+    float f = ((float)pos - c0) * inv_s;
     f = fminf(fmaxf(f, 0.f), (float)(n - 1));
     int ia = (int)floorf(f);
     if (ia > n - 2) ia = n - 2;
     i0 = ia;
     t = f - (float)ia;
 }
-
-constexpr int NROW_CAP = DTY / 3 + 4;  // node rows a tile touches (steps >= 3, checked on the host)
 
 __device__ __forceinline__ float warp_min(float v)
 {
@@ -54,51 +55,73 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
+// Exact float of a pixel: integers below 2^23 placed in the mantissa under the
+// exponent of 2^23, minus 2^23 (two full-rate instructions instead of a
+// conversion).
+__device__ __forceinline__ float pix(uint8_t v) { return __uint_as_float(0x4B000000u | (uint32_t)v) - 8388608.f; }
+__device__ __forceinline__ float pix(uint16_t v) { return __uint_as_float(0x4B000000u | (uint32_t)v) - 8388608.f; }
+__device__ __forceinline__ float pix(float v) { return v; }
+
+// floor of d (|d| < 2^22) as a float and as an int: the integer of the floored
+// value read from the mantissa of fl + 1.5 * 2^23
+__device__ __forceinline__ void floor_split(float d, float &fl, int &i)
+{
+    fl = floorf(d);
+    i = __float_as_int(fl + 12582912.f) - 0x4B400000;
+}
+
 // The tile in slices of 32 rows; within a slice all rows of a thread are
 // unrolled so that their gathers are in flight together; rows and columns
 // past the grown image are computed on clamped coordinates and not stored.
-// Off: the integer type of pixel offsets.
-template <typename T, typename Off>
-__device__ __forceinline__ void deform_rows(const DeformArgs &a, const unsigned char *img, float *out, bool has,
-                                            bool inside, int dj, Off pe, int x, int y0, int lx, int ly0,
-                                            const float (*cu)[DTX], const float (*cv)[DTX], const int *riy,
-                                            const float *rty)
+// CLAMP: the taps are clamped to the image (tiles near its border or with a
+// displacement range reaching outside); otherwise the four taps of a pixel
+// are read from one base pointer.  Off: the integer type of pixel offsets.
+template <typename T, typename Off, bool CLAMP>
+__device__ __forceinline__ void deform_rows(const DeformArgs &a, const T *base, float *out, int djo, Off pe, int x,
+                                            int y0, int lx, int ly0, const float2 *cuv, const int2 *rinfo)
 {
-    const T *base = reinterpret_cast<const T *>(img);
+    // warps whose 32 columns, and slices whose 32 rows, lie past the grown
+    // image store nothing: skip them (uniform per warp)
+    if (x - (int)(threadIdx.x & 31) >= a.W + a.M) return;
     for (int half = 0; half < DTY / 32; ++half) {
+        if (y0 + 32 * half >= a.H + a.M) break;
         float res[DROWS];
 #pragma unroll
         for (int k = 0; k < DROWS; ++k) {
             const int ly = 32 * half + ly0 + 4 * k, y = y0 + ly;
-            float du = 0.f, dv = 0.f;
-            if (has) {
-                const int j0 = riy[ly];
-                const float ty = rty[ly];
-                const float u0 = cu[j0][lx], u1 = cu[j0 + dj][lx];
-                const float v0 = cv[j0][lx], v1 = cv[j0 + dj][lx];
-                du = a.scale * (u0 + ty * (u1 - u0));
-                dv = a.scale * (v0 + ty * (v1 - v0));
-                if (!inside) {
-                    // NaN or absurd predictor values are clamped so the index math cannot overflow
-                    du = fminf(fmaxf(du, -1048576.f), 1048576.f);
-                    dv = fminf(fmaxf(dv, -1048576.f), 1048576.f);
-                }
+            const int2 ri = rinfo[ly];
+            const float ty = __int_as_float(ri.y);
+            const float2 n0 = cuv[ri.x + lx], n1 = cuv[ri.x + djo + lx];
+            float du = fmaf(ty, n1.x - n0.x, n0.x), dv = fmaf(ty, n1.y - n0.y, n0.y);
+            if (CLAMP) {
+                // NaN or absurd predictor values are clamped so the index math cannot overflow
+                du = fminf(fmaxf(du, -1048576.f), 1048576.f);
+                dv = fminf(fmaxf(dv, -1048576.f), 1048576.f);
             }
-            const float fx = floorf(du), fy = floorf(dv);
-            const float tx = du - fx, ty = dv - fy;
-            int xa = x + (int)fx, ya = y + (int)fy;
-            int xb = xa + 1, yb = ya + 1;
-            if (!inside) {
-                xb = min(max(xb, 0), a.W - 1);
-                yb = min(max(yb, 0), a.H - 1);
-                xa = min(max(xa, 0), a.W - 1);
-                ya = min(max(ya, 0), a.H - 1);
+            float fx, fy;
+            int ix, iy;
+            floor_split(du, fx, ix);
+            floor_split(dv, fy, iy);
+            const float tx = du - fx, tyy = dv - fy;
+            float b00, b10, b01, b11;
+            if (CLAMP) {
+                const int xl = x + ix, yl = y + iy;
+                const int xa = min(max(xl, 0), a.W - 1), xb = min(max(xl + 1, 0), a.W - 1);
+                const int ya = min(max(yl, 0), a.H - 1), yb = min(max(yl + 1, 0), a.H - 1);
+                const T *ra = base + (Off)ya * pe, *rb = base + (Off)yb * pe;
+                b00 = pix(__ldg(ra + xa));
+                b10 = pix(__ldg(ra + xb));
+                b01 = pix(__ldg(rb + xa));
+                b11 = pix(__ldg(rb + xb));
+            } else {
+                const T *q = base + ((Off)(y + iy) * pe + (Off)(x + ix));
+                b00 = pix(__ldg(q));
+                b10 = pix(__ldg(q + 1));
+                b01 = pix(__ldg(q + pe));
+                b11 = pix(__ldg(q + pe + 1));
             }
-            const T *rowa = base + (Off)ya * pe, *rowb = base + (Off)yb * pe;
-            const float b00 = (float)__ldg(rowa + xa), b10 = (float)__ldg(rowa + xb);
-            const float b01 = (float)__ldg(rowb + xa), b11 = (float)__ldg(rowb + xb);
             const float top = b00 + tx * (b10 - b00), bot = b01 + tx * (b11 - b01);
-            res[k] = top + ty * (bot - top);
+            res[k] = top + tyy * (bot - top);
         }
         if (x < a.W + a.M) {
             float *o = out + (long long)(y0 + 32 * half + ly0 + a.M) * a.out_pitch + (x + a.M);
@@ -111,36 +134,47 @@ __device__ __forceinline__ void deform_rows(const DeformArgs &a, const unsigned 
     }
 }
 
+template <typename T, typename Off>
+__device__ __forceinline__ void deform_rows_any(const DeformArgs &a, const T *base, float *out, bool inside, int djo,
+                                                Off pe, int x, int y0, int lx, int ly0, const float2 *cuv,
+                                                const int2 *rinfo)
+{
+    if (inside)
+        deform_rows<T, Off, false>(a, base, out, djo, pe, x, y0, lx, ly0, cuv, rinfo);
+    else
+        deform_rows<T, Off, true>(a, base, out, djo, pe, x, y0, lx, ly0, cuv, rinfo);
+}
+
 // The field is bilinear in the nodes: the tile first interpolates every node
-// row it touches along x at each of its columns (cu, cv), so that a pixel
-// needs one interpolation along y.  A tile whose taps provably stay inside
-// the image (its displacement lies within the range of its nodes, a convex
-// combination) skips the clamping; either way every tap is the clamp-to-edge
-// sample.
+// row it touches along x at each of its columns, already scaled (cuv), and
+// stores per row its node-row offset and weight (rinfo), so that a pixel needs
+// one interpolation along y.  A tile whose taps provably stay inside the image
+// (its displacement lies within the range of its nodes, a convex combination)
+// skips the clamping; either way every tap is the clamp-to-edge sample.
 template <typename T>
 __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const float *pu, const float *pv,
                             float *out)
 {
     __shared__ float nu[NODE_CAP], nv[NODE_CAP];
-    __shared__ float cu[NROW_CAP][DTX], cv[NROW_CAP][DTX];
-    __shared__ int riy[DTY];
-    __shared__ float rty[DTY];
+    __shared__ float2 cuv[NROW_CAP * DTX];
+    __shared__ int2 rinfo[DTY];
     __shared__ float red[4][8];
     const int x0 = blockIdx.x * DTX - a.M, y0 = blockIdx.y * DTY - a.M;
-    const float c0 = 0.5f * (float)(a.w - 1);
+    const float c0 = 0.5f * (float)(a.w - 1), inv_s = 1.f / (float)a.s;
     const bool has = pu != nullptr && pv != nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = threadIdx.x % DTX, ly0 = threadIdx.x / DTX;
     const int x = x0 + lx;
     float umin = 0.f, umax = 0.f, vmin = 0.f, vmax = 0.f;
     bool any_nan = false;
+    int djo = 0;
     if (has) {
         int ilo, ihi, jlo, jhi;
         float t;
-        axis_weight(x0, a.nx, c0, a.s, ilo, t);
-        axis_weight(x0 + DTX - 1, a.nx, c0, a.s, ihi, t);
-        axis_weight(y0, a.ny, c0, a.s, jlo, t);
-        axis_weight(y0 + DTY - 1, a.ny, c0, a.s, jhi, t);
+        axis_weight(x0, a.nx, c0, inv_s, ilo, t);
+        axis_weight(x0 + DTX - 1, a.nx, c0, inv_s, ihi, t);
+        axis_weight(y0, a.ny, c0, inv_s, jlo, t);
+        axis_weight(y0 + DTY - 1, a.ny, c0, inv_s, jhi, t);
         ihi = min(ihi + 1, a.nx - 1);
         jhi = min(jhi + 1, a.ny - 1);
         const int nwn = ihi - ilo + 1, nhn = jhi - jlo + 1;
@@ -169,21 +203,20 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
         }
         for (int e = threadIdx.x; e < DTY; e += blockDim.x) {
             int j0;
-            axis_weight(y0 + e, a.ny, c0, a.s, j0, t);
-            riy[e] = j0 - jlo;
-            rty[e] = t;
+            axis_weight(y0 + e, a.ny, c0, inv_s, j0, t);
+            rinfo[e] = make_int2((j0 - jlo) * DTX, __float_as_int(t));
         }
         any_nan = __syncthreads_or(nan_seen);
-        // node rows interpolated along x at this thread's column
+        // node rows interpolated along x at this thread's column, scaled
         {
             int i0;
             float tx;
-            axis_weight(x, a.nx, c0, a.s, i0, tx);
+            axis_weight(x, a.nx, c0, inv_s, i0, tx);
             const int ci = i0 - ilo, di = a.nx > 1 ? 1 : 0;
             for (int jj = ly0; jj < nhn; jj += blockDim.x / DTX) {
                 const float *ru = nu + jj * nwn + ci, *rv = nv + jj * nwn + ci;
-                cu[jj][lx] = ru[0] + tx * (ru[di] - ru[0]);
-                cv[jj][lx] = rv[0] + tx * (rv[di] - rv[0]);
+                cuv[jj * DTX + lx] = make_float2(a.scale * (ru[0] + tx * (ru[di] - ru[0])),
+                                                 a.scale * (rv[0] + tx * (rv[di] - rv[0])));
             }
         }
         umin = red[0][0];
@@ -202,6 +235,12 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
         umax = fmaxf(su0, su1);
         vmin = fminf(sv0, sv1);
         vmax = fmaxf(sv0, sv1);
+        djo = a.ny > 1 ? DTX : 0;
+        __syncthreads();
+    } else {
+        // no predictor: one zero node row, weight 0 on every row
+        if (threadIdx.x < DTX) cuv[threadIdx.x] = make_float2(0.f, 0.f);
+        if (threadIdx.x < DTY) rinfo[threadIdx.x] = make_int2(0, 0);
         __syncthreads();
     }
     // every tap of the tile inside the image, with a pixel to spare against rounding
@@ -209,13 +248,13 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
                         vmax < 1048576.f && x0 + floorf(umin) - 1.f >= 0.f &&
                         x0 + DTX - 1 + floorf(umax) + 2.f <= (float)(a.W - 1) && y0 + floorf(vmin) - 1.f >= 0.f &&
                         y0 + DTY - 1 + floorf(vmax) + 2.f <= (float)(a.H - 1);
-    const int dj = a.ny > 1 ? 1 : 0;
+    const T *base = reinterpret_cast<const T *>(img);
     const long long pe = a.pitch / (long long)sizeof(T);  // row pitch in pixels (a multiple of the pixel size)
     // 32-bit pixel offsets when the whole image fits them
     if ((long long)a.H * pe < (1LL << 31))
-        deform_rows<T, int>(a, img, out, has, inside, dj, (int)pe, x, y0, lx, ly0, cu, cv, riy, rty);
+        deform_rows_any<T, int>(a, base, out, inside, djo, (int)pe, x, y0, lx, ly0, cuv, rinfo);
     else
-        deform_rows<T, long long>(a, img, out, has, inside, dj, pe, x, y0, lx, ly0, cu, cv, riy, rty);
+        deform_rows_any<T, long long>(a, base, out, inside, djo, pe, x, y0, lx, ly0, cuv, rinfo);
 }
 
 // one kernel per pixel type, so that each holds a single copy of the tile's

@@ -6,15 +6,19 @@
 // Work of one CTA, staged in shared memory:
 //   A region   A - mu_T over the union of the tile's windows (aw x ah)
 //   B' region  B' - mu_T over the A region grown by R+1 on each side
-//   C, V       sliding box sums of B' and B'^2: V[r][c] is the sum over the
-//              w x w box with top-left logical B' pixel (r, c), i.e. the sums
-//              of every window at every shift in [-R-1, R+1]^2, by lookup
-//   P          block partial planes: the A region is cut into G x G blocks
-//              (G = gcd(w, s)); P_b(s) = sum_{x in b} A_c(x) B'_c(x + s).
+//   C, V       sliding box sums of B' and B'^2 (C: columns, V: rows); V1[r][c]
+//              is the sum of B' over the w x w box with top-left logical B'
+//              pixel (r, c), VN[r][c] = 1 / sqrt(E_B) of that box (0 when the
+//              box is degenerate), i.e. every window at every shift in
+//              [-R-1, R+1]^2, by lookup
+//   P          block planes: the A region is cut into G x G blocks
+//              (G = gcd(w, s)); P_b(s) = sum_{x in b} A(x) B'(x + s).
 //              A window's numerator is the sum of its (w/G)^2 block planes
-//              minus mean(A_c) * sum B'_c(x + s); this regrouping is exact,
-//              and computes each block once instead of once per overlapping
-//              window.
+//              minus mean(A) * V1(s); this regrouping is exact, and computes
+//              each block once instead of once per overlapping window.
+// The peak is searched on C(s) sqrt(E_A) = numerator(s) VN(s): a positive
+// per-window scale leaves the argmax unchanged; the five stencil values are
+// scaled back by 1 / sqrt(E_A) before the fit.
 // The planes are formed with FP32 FMAs on the CUDA cores, or with BF16/FP16
 // tensor-core MMAs (mma.sync m16n8k8, FP32 accumulate) whose accumulator tile
 // D[i][j] (i = B' row, j = A row of an 8-row sub-block) carries shift
@@ -113,13 +117,17 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// one bounded poll: the thread may sleep up to MBAR_SUSPEND_NS until the phase
+// completes, so the wait costs few issue slots
+constexpr uint32_t MBAR_SUSPEND_NS = 256;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(MBAR_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -200,11 +208,19 @@ __device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, 
 
 // ------------------------------------------------------ box sums (C, V) --
 
+// 1 / sqrt(E_B) of a box from its sum and sum of squares; 0 for a degenerate box
+__device__ __forceinline__ float inv_norm(float s1, float s2, float inv_n, float tau)
+{
+    const float EB = s2 - s1 * s1 * inv_n;
+    return EB > tau ? rsqrtf(EB) : 0.f;
+}
+
 // Window box sums of B' and B'^2 at every shift, in two sliding passes:
 //   C[r][x] = sum_{y=r}^{r+w-1} B'[y][x]        (threads along x: conflict free)
 //   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]         (threads along r, odd pitch)
 // so V[r][c] is the sum over the w x w box whose top-left logical B' pixel
-// is (r, c).  Each thread restarts its running sum every 8 outputs.
+// is (r, c); the second plane keeps 1 / sqrt(E_B) of the box instead of its
+// sum of squares.  Each thread restarts its running sum every 8 outputs.
 static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
 {
     const PassPlan &P = a.plan;
@@ -234,7 +250,8 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
     }
     __syncthreads();
     const int vp = P.v_pitch;  // pitch of V (odd, >= hw)
-    float *V1 = Vs, *V2 = Vs + g.vh * vp;
+    const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
+    float *V1 = Vs, *VN = Vs + g.vh * vp;
     const int nsegh = (g.hw + 7) / 8;
     for (int it = tid; it < g.vh * nsegh; it += blockDim.x) {
         const int seg = it / g.vh, r = it - seg * g.vh;
@@ -246,20 +263,64 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
             s2 += c2[x];
         }
         V1[r * vp + c_lo] = s1;
-        V2[r * vp + c_lo] = s2;
+        VN[r * vp + c_lo] = inv_norm(s1, s2, inv_n, tau);
         for (int c = c_lo + 1; c < c_hi; ++c) {
             s1 += c1[c + w - 1] - c1[c - 1];
             s2 += c2[c + w - 1] - c2[c - 1];
             V1[r * vp + c] = s1;
-            V2[r * vp + c] = s2;
+            VN[r * vp + c] = inv_norm(s1, s2, inv_n, tau);
         }
     }
 }
 
-// Sum and centred sum of squares of every G x G block of A (two passes; one
-// warp per block, lanes along the rows): bst[b] = (sum, M2).
+// Sum and centred sum of squares of every G x G block of A (two passes):
+// bst[b] = (sum, M2).  For G a power of two from 4 to 32 one thread takes a
+// block row (128-bit loads) and the G rows of a block, in aligned lanes of one
+// warp, are summed by shuffles; the mean is exact scaling by 1 / G^2.
+static __device__ __forceinline__ void block_stats_rows(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
+{
+    const PassPlan &P = a.plan;
+    const int lane = threadIdx.x & 31;
+    const int G = g.G, lg = __ffs(G) - 1;
+    const float inv_n = 1.f / (float)(G * G);
+    const int items = g.nb * G;
+    // warp-uniform trip count: every lane takes part in the shuffles; lanes
+    // past the end repeat the last row and store nothing
+    for (int base = threadIdx.x - lane; base < items; base += blockDim.x) {
+        const int it = min(base + lane, items - 1);
+        const int b = it >> lg, row = it & (G - 1);
+        const int byi = b / g.nbx, bxi = b - byi * g.nbx;
+        const float *p = As + (byi * G + row) * P.a_pitch + bxi * G;
+        float s = 0.f;
+        for (int c = 0; c < G; c += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + c);
+            s += v.x;
+            s += v.y;
+            s += v.z;
+            s += v.w;
+        }
+        for (int o = 1; o < G; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float m = s * inv_n;
+        float q = 0.f;
+        for (int c = 0; c < G; c += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + c);
+            q = fmaf(v.x - m, v.x - m, q);
+            q = fmaf(v.y - m, v.y - m, q);
+            q = fmaf(v.z - m, v.z - m, q);
+            q = fmaf(v.w - m, v.w - m, q);
+        }
+        for (int o = 1; o < G; o <<= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (base + lane < items && row == 0) bst[b] = make_float2(s, q);
+    }
+}
+
+// Any G: one warp per block, lanes along the rows.
 static __device__ __forceinline__ void block_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
 {
+    if (g.G >= 4 && g.G <= 32 && (g.G & (g.G - 1)) == 0) {
+        block_stats_rows(a, g, As, bst);
+        return;
+    }
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int G = g.G;
@@ -309,6 +370,20 @@ static __device__ __forceinline__ void window_stats(const PassArgs &a, const Til
 
 // --------------------------------------------- FP32 block planes (CUDA cores) --
 
+// Plane items are (unit, row group) with RG a power of two: a warp takes
+// 32 / RG consecutive units, the row group in the high lane bits, so that a
+// quarter-warp reads consecutive shifts (bank-conflict free) and a butterfly of
+// shuffles over lane distances 32 / RG, ... , 16 sums a unit's partials; row
+// group 0 stores the sum.
+template <int ND>
+__device__ __forceinline__ void sum_row_groups(float (&acc)[ND], int lrg)
+{
+    for (int o = 32 >> lrg; o < 32; o <<= 1) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+    }
+}
+
 // Compile-time radius: each thread owns one (block, sy, row group) and keeps
 // the 2R+1 accumulators of its sx row in registers; rows are streamed from
 // shared memory four columns at a time with aligned 128-bit loads.
@@ -316,18 +391,19 @@ template <int R>
 __device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, float *Ps)
 {
     constexpr int ND = 2 * R + 1;
-    constexpr int NP = ND * ND;
     constexpr int MIS = ((-R) % 4 + 4) % 4;
     constexpr int NQ = (4 + 2 * R + MIS + 3) / 4;
     const PassPlan &P = a.plan;
-    const int G = g.G, RG = P.RGx, rows = G / RG;
-    const int items = g.nb * ND * RG;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int syi = it % ND;
-        const int rest = it / ND;
-        const int gi = rest % RG;
-        const int b = rest / RG;
-        const int bxi = b % g.nbx, byi = b / g.nbx;
+    const int G = g.G, RG = P.RGx, rows = G / RG, lrg = __ffs(RG) - 1;
+    const int units = g.nb * ND;  // (block, sy)
+    const int lane = threadIdx.x & 31, gi = lane >> (5 - lrg), ul = lane & ((32 >> lrg) - 1);
+    // warp-uniform trip count for the shuffles; lanes past the last unit
+    // repeat it and store nothing
+    for (int base = (threadIdx.x - lane) >> lrg; base < units; base += blockDim.x >> lrg) {
+        const int u = min(base + ul, units - 1);
+        const int b = u / ND;
+        const int syi = u - b * ND;
+        const int byi = b / g.nbx, bxi = b - byi * g.nbx;
         const int c0 = bxi * G, r0 = byi * G + gi * rows;
         float acc[ND];
 #pragma unroll
@@ -354,9 +430,12 @@ __device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileG
                 }
             }
         }
-        float *out = Ps + (size_t)(b * RG + gi) * NP + syi * ND;
+        sum_row_groups<ND>(acc, lrg);
+        if (base + ul < units && gi == 0) {
+            float *out = Ps + b * P.pstride + syi * ND;
 #pragma unroll
-        for (int d = 0; d < ND; ++d) out[d] = acc[d];
+            for (int d = 0; d < ND; ++d) out[d] = acc[d];
+        }
     }
 }
 
@@ -365,18 +444,17 @@ static __device__ __forceinline__ void block_planes_fp32_generic(const PassArgs 
                                           float *Ps)
 {
     const PassPlan &P = a.plan;
-    const int R = g.R, ND = g.ND, NP = g.NP;
-    const int G = g.G, RG = P.RGx, rows = G / RG;
+    const int R = g.R, ND = g.ND;
+    const int G = g.G, RG = P.RGx, rows = G / RG, lrg = __ffs(RG) - 1;
     const int nch = (ND + 7) / 8;
-    const int items = g.nb * ND * RG * nch;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        int rest = it;
+    const int units = g.nb * ND * nch;  // (block, sy, sx chunk)
+    const int lane = threadIdx.x & 31, gi = lane >> (5 - lrg), ul = lane & ((32 >> lrg) - 1);
+    for (int base = (threadIdx.x - lane) >> lrg; base < units; base += blockDim.x >> lrg) {
+        int rest = min(base + ul, units - 1);
         const int ch = rest % nch;
         rest /= nch;
         const int syi = rest % ND;
-        rest /= ND;
-        const int gi = rest % RG;
-        const int b = rest / RG;
+        const int b = rest / ND;
         const int bxi = b % g.nbx, byi = b / g.nbx;
         const int c0 = bxi * G, r0 = byi * G + gi * rows;
         const int d0 = ch * 8;
@@ -393,8 +471,11 @@ static __device__ __forceinline__ void block_planes_fp32_generic(const PassArgs 
                     if (d0 + d < ND) acc[d] = fmaf(av, brow[c + d], acc[d]);
             }
         }
-        float *out = Ps + (size_t)(b * RG + gi) * NP + syi * ND + d0;
-        for (int d = 0; d < 8 && d0 + d < ND; ++d) out[d] = acc[d];
+        sum_row_groups<8>(acc, lrg);
+        if (base + ul < units && gi == 0) {
+            float *out = Ps + b * P.pstride + syi * ND + d0;
+            for (int d = 0; d < 8 && d0 + d < ND; ++d) out[d] = acc[d];
+        }
     }
 }
 
@@ -523,7 +604,7 @@ __device__ __forceinline__ void block_planes_tc(const PassArgs &a, const TileGeo
             }
         }
         // D[m][n] of tile (mt, nt) is P_b(sy = 8 nt + n - R, sx = 16 mt + m - R)
-        float *out = Ps + (size_t)(b * RG + gi) * NP;
+        float *out = Ps + b * P.pstride + gi * NP;
 #pragma unroll
         for (int m = 0; m < MT; ++m)
 #pragma unroll
@@ -537,14 +618,31 @@ __device__ __forceinline__ void block_planes_tc(const PassArgs &a, const TileGeo
     }
 }
 
+// Tensor-core path with RG > 1: the row groups' partial planes of a block
+// (consecutive, NP floats apart) are summed into the first, in a fixed order.
+static __device__ __forceinline__ void reduce_row_groups(const PassArgs &a, const TileGeom &g, float *Ps)
+{
+    const int RG = a.plan.RGx, NP = g.NP, ps = a.plan.pstride;
+    for (int e = threadIdx.x; e < g.nb * NP; e += blockDim.x) {
+        const int b = e / NP, q = e - b * NP;
+        float *p = Ps + b * ps + q;
+        float v = p[0];
+        for (int t = 1; t < RG; ++t) v += p[t * NP];
+        p[0] = v;
+    }
+}
+
 // ----------------------------------------------- assembly and sub-pixel --
 
-__device__ __forceinline__ float gauss3f(float cm, float c0, float cp)
+// Three-point Gaussian fit on a log scale, with the parabola as a fallback;
+// lm, l0, lp are the logs of the values that are positive (only used when
+// all three are).  Both forms are unchanged when the three values share a
+// positive factor.
+__device__ __forceinline__ float gauss3f(float cm, float c0, float cp, float lm, float l0, float lp)
 {
     float d = 0.f;
     bool ok = false;
     if (cm > 0.f && c0 > 0.f && cp > 0.f) {
-        const float lm = logf(cm), l0 = logf(c0), lp = logf(cp);
         const float den = 2.f * lm - 4.f * l0 + 2.f * lp;
         if (den < 0.f) {
             d = (lm - lp) / den;
@@ -562,14 +660,55 @@ __device__ __forceinline__ float gauss3f(float cm, float c0, float cp)
     return fminf(fmaxf(d, -1.f), 1.f);
 }
 
-// ZNCC from the numerator sum A_c B'_c, the window's mean/energy of A_c and
-// the box sums of B'_c at this shift; degenerate windows give 0.
-__device__ __forceinline__ float zncc_from(float num, float muA, float EA, float S1, float S2, float inv_n, float tau)
+// C(s) sqrt(E_A) from the numerator sum A B' over the window, its mean of A and
+// the box's sum S1 and 1 / sqrt(E_B); a degenerate box gives +0.
+__device__ __forceinline__ float scaled_zncc(float num, float muA, float S1, float nB)
 {
-    const float Nc = num - muA * S1;
-    const float EB = S2 - S1 * S1 * inv_n;
-    if (!(EA > tau) || !(EB > tau)) return 0.f;
-    return Nc * rsqrtf(EA * EB);
+    return (num - muA * S1) * nB + 0.f;
+}
+
+// Order-preserving key of a float that is not NaN (-0 and +0 are equal once
+// canonicalised by scaled_zncc); 0 is left for "no value".
+__device__ __forceinline__ uint32_t ord_key(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float log_pos(float c) { return c > 0.f ? logf(c) : 0.f; }
+
+// Outputs of one window: predictor + integer peak + sub-pixel offsets, the
+// info word (bit 0 valid, ky and kx as int8 in bits 8..15 and 16..23); a
+// degenerate window passes the predictor through with info 0.
+struct WinOut {
+    const PassArgs *a;  // the kernel's parameters: pointers are read at the write
+    int pair;
+    __device__ __forceinline__ void put(int k, bool ok, int ky, int kx, float dx, float dy) const
+    {
+        const float *pu = (const float *)resolve(a->pred_u, pair);
+        const float *pv = (const float *)resolve(a->pred_v, pair);
+        float *ou = (float *)resolve(a->out_u, pair);
+        float *ov = (float *)resolve(a->out_v, pair);
+        int32_t *oi = (int32_t *)resolve(a->out_info, pair);
+        const float pu0 = pu ? pu[k] : 0.f, pv0 = pv ? pv[k] : 0.f;
+        if (!ok) {
+            ou[k] = pu0;
+            ov[k] = pv0;
+            oi[k] = 0;
+            return;
+        }
+        ou[k] = pu0 + (float)kx + dx;
+        ov[k] = pv0 + (float)ky + dy;
+        oi[k] = 1 | ((int)(uint8_t)(int8_t)ky << 8) | ((int)(uint8_t)(int8_t)kx << 16);
+    }
+};
+
+__device__ __forceinline__ WinOut win_out(const PassArgs &a, int pair)
+{
+    WinOut o;
+    o.a = &a;
+    o.pair = pair;
+    return o;
 }
 
 __device__ __forceinline__ void stencil_shift(int p, int ky, int kx, int &sy, int &sx)
@@ -580,16 +719,20 @@ __device__ __forceinline__ void stencil_shift(int p, int ky, int kx, int &sy, in
 }
 
 struct WinShared {
-    float *c5;    // [nwin][5] stencil values (plane-supplied ones)
+    float *c5;    // [nwin][5] stencil values (plane-supplied ones), scaled by sqrt(E_A)
     int *peaks;   // [nwin] plane index of the argmax
     int *need;    // [nwin] bit p set: stencil point p needs a direct FP32 sum
     float *dpart; // [nwin][ngr][5] direct numerators per 8-row group
 };
 
-// One warp per window: plane from the block planes and box sums, argmax
-// (ties keep the smallest row-major index), plane values of the stencil.
-// RC >= 0: compile-time radius (shift decoding without integer division).
-template <int RC>
+// One warp per window: scaled plane from the block planes and box sums, argmax
+// (ties keep the smallest row-major index) by two warp reductions, plane values
+// of the stencil.  Degenerate windows (E_A <= tau) are skipped: the finalize
+// step passes the predictor through for them.
+// RC >= 0: compile-time radius; each lane decodes the shifts it owns
+// (q = lane + 32 j) once, into plane and box-sum offsets kept in registers.
+// ONE_PLANE: one plane per block (FP32 planes), so the block stride is NP.
+template <int RC, bool ONE_PLANE>
 static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
                                       const float *stats, bool tc, const WinShared &ws)
 {
@@ -597,60 +740,80 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int R = RC >= 0 ? RC : g.R;
     const int ND = 2 * R + 1, NP = ND * ND;
-    const int G = g.G, kb = g.w / G, RG = P.RGx;
-    const float inv_n = 1.f / (float)(g.w * g.w), tau = TAU_PER_PIXEL * (float)(g.w * g.w);
+    const int kb = g.kb, sg = g.s / g.G;  // blocks per window side, per step
+    const int ps = ONE_PLANE ? NP : P.pstride, rs = g.nbx * ps;
+    const float tau = TAU_PER_PIXEL * (float)(g.w * g.w);
     const int cp = P.v_pitch;
-    const float *V1 = Vs, *V2 = Vs + g.vh * cp;
-    for (int wi = warp; wi < g.nwin; wi += nwarps) {
-        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
-        const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
-        const int bx0 = (wxi * g.s) / G, by0 = (wyi * g.s) / G;
-        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
-        const float *v2 = V2 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
-        // the window's partial planes: for each of its kb block rows, kb * RG
-        // consecutive planes of NP floats
-        const float *prow = Ps + (size_t)(by0 * g.nbx + bx0) * RG * NP;
-        const int run = kb * RG, row_stride = g.nbx * RG * NP;
-        auto cval = [&](int q) {
-            const int qy = q / ND;
-            const int sy = qy - R, sx = q - qy * ND - R;
-            float num = 0.f;
-            for (int yy = 0; yy < kb; ++yy) {
-                const float *pr = prow + (size_t)yy * row_stride + q;
-                for (int t = 0; t < run; ++t) num += pr[t * NP];
-            }
-            const float S1 = v1[sy * cp + sx], S2 = v2[sy * cp + sx];
-            const float Nc = num - muA * S1;
-            const float EB = S2 - S1 * S1 * inv_n;
-            if (!(EA > tau) || !(EB > tau)) return 0.f;
-            return Nc * rsqrtf(EA * EB);
-        };
-        float best = -INFINITY;
-        int bidx = 0x7fffffff;
-        for (int q = lane; q < NP; q += 32) {
-            const float c = cval(q);
-            if (c > best || (c == best && q < bidx)) {
-                best = c;
-                bidx = q;
-            }
-        }
+    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    constexpr uint32_t NONE = 0xffffffffu;
+    // shifts owned by this lane: plane offset q and box-sum offset, per j
+    constexpr int NQ = RC >= 0 ? ((2 * RC + 1) * (2 * RC + 1) + 31) / 32 : 1;
+    int qv[NQ], vv[NQ];
+    if (RC >= 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oq = __shfl_xor_sync(0xffffffffu, bidx, o);
-            if (ob > best || (ob == best && oq < bidx)) {
-                best = ob;
-                bidx = oq;
+        for (int j = 0; j < NQ; ++j) {
+            const int q = min(lane + 32 * j, NP - 1);
+            const int qy = q / ND, qx = q - qy * ND;
+            qv[j] = q;
+            vv[j] = (qy - R) * cp + (qx - R);
+        }
+    }
+    auto block_sum = [&](const float *pb, int q) {
+        float num = 0.f;
+        for (int yy = 0; yy < kb; ++yy)
+            for (int xx = 0; xx < kb; ++xx) num += pb[yy * rs + xx * ps + q];
+        return num;
+    };
+    for (Walk2D wk(warp, nwarps, g.nwx); wk.y < g.nwy; wk.next()) {
+        const int wxi = wk.x, wyi = wk.y, wi = wyi * g.nwx + wxi;
+        const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
+        if (!(EA > tau)) {
+            if (lane == 0) {
+                ws.peaks[wi] = NP / 2;
+                ws.need[wi] = 0;
+            }
+            continue;
+        }
+        const float *pb = Ps + (wyi * sg * g.nbx + wxi * sg) * ps;
+        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        float best = 0.f;
+        uint32_t bq = NONE;
+        // ascending q: the first of equal values stays; NaN never wins
+        auto offer = [&](float c, int q) {
+            if (c > best || (bq == NONE && c == c)) {
+                best = c;
+                bq = (uint32_t)q;
+            }
+        };
+        if (RC >= 0) {
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                if (j < NQ - 1 || lane + 32 * j < NP)
+                    offer(scaled_zncc(block_sum(pb, qv[j]), muA, v1[vv[j]], vn[vv[j]]), qv[j]);
+            }
+        } else {
+            for (int q = lane; q < NP; q += 32) {
+                const int qy = q / ND, vo = (qy - R) * cp + (q - qy * ND - R);
+                offer(scaled_zncc(block_sum(pb, q), muA, v1[vo], vn[vo]), q);
             }
         }
-        if (bidx < 0 || bidx >= NP) bidx = NP / 2;  // non-finite plane: zero shift
+        const uint32_t key = bq == NONE ? 0u : ord_key(best);
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+        const uint32_t qmin = __reduce_min_sync(0xffffffffu, (key == kmax && bq != NONE) ? bq : NONE);
+        const int bidx = qmin < (uint32_t)NP ? (int)qmin : NP / 2;  // no finite value: zero shift
         const int ky = bidx / ND - R, kx = bidx % ND - R;
         if (lane < 5) {
             int sy, sx;
             stencil_shift(lane, ky, kx, sy, sx);
             const bool inside = sy >= -R && sy <= R && sx >= -R && sx <= R;
             const bool direct = tc || !inside;
-            ws.c5[wi * 5 + lane] = direct ? 0.f : cval((sy + R) * ND + (sx + R));
+            float c = 0.f;
+            if (!direct) {
+                const int q = (sy + R) * ND + (sx + R), vo = sy * cp + sx;
+                c = scaled_zncc(block_sum(pb, q), muA, v1[vo], vn[vo]);
+            }
+            ws.c5[wi * 5 + lane] = c;
             const unsigned bits = __ballot_sync(0x1fu, direct);
             if (lane == 0) {
                 ws.peaks[wi] = bidx;
@@ -707,46 +870,41 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
 {
     const PassPlan &P = a.plan;
     const int w = g.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
-    const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
     const int cp = P.v_pitch;
-    const float *V1 = Vs, *V2 = Vs + g.vh * cp;
-    const float *pu = (const float *)resolve(a.pred_u, pair);
-    const float *pv = (const float *)resolve(a.pred_v, pair);
-    float *ou = (float *)resolve(a.out_u, pair);
-    float *ov = (float *)resolve(a.out_v, pair);
-    int32_t *oi = (int32_t *)resolve(a.out_info, pair);
+    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    const WinOut out = win_out(a, pair);
+    const float tau = TAU_PER_PIXEL * (float)(w * w);
     for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
-        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
+        const int wyi = wi / g.nwx, wxi = wi - wyi * g.nwx;
         const int k = (g.wy0 + wyi) * a.nx + (g.wx0 + wxi);
-        const float pu0 = pu ? pu[k] : 0.f, pv0 = pv ? pv[k] : 0.f;
         const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
         if (!(EA > tau)) {
-            ou[k] = pu0;
-            ov[k] = pv0;
-            oi[k] = 0;
+            out.put(k, false, 0, 0, 0.f, 0.f);
             continue;
         }
         const int q = ws.peaks[wi], need = ws.need[wi];
         const int ky = q / ND - R, kx = q % ND - R;
-        float c5[5];
+        const float inv_a = rsqrtf(EA);
+        float c5[5], l5[5];
 #pragma unroll
         for (int p = 0; p < 5; ++p) {
+            float c;
             if (need & (1 << p)) {
                 int sy, sx;
                 stencil_shift(p, ky, kx, sy, sx);
                 float num = 0.f;
                 for (int gr = 0; gr < ngr; ++gr) num += ws.dpart[(wi * ngr + gr) * 5 + p];
                 const int vo = (wyi * g.s + R + 1 + sy) * cp + wxi * g.s + R + 1 + sx;
-                c5[p] = zncc_from(num, muA, EA, V1[vo], V2[vo], inv_n, tau);
+                c = scaled_zncc(num, muA, V1[vo], VN[vo]);
             } else {
-                c5[p] = ws.c5[wi * 5 + p];
+                c = ws.c5[wi * 5 + p];
             }
+            c5[p] = c * inv_a;
+            l5[p] = log_pos(c5[p]);
         }
-        const float dx = gauss3f(c5[1], c5[0], c5[2]);
-        const float dy = gauss3f(c5[3], c5[0], c5[4]);
-        ou[k] = pu0 + (float)kx + dx;
-        ov[k] = pv0 + (float)ky + dy;
-        oi[k] = 1 | ((int)(uint8_t)(int8_t)ky << 8) | ((int)(uint8_t)(int8_t)kx << 16);
+        const float dx = gauss3f(c5[1], c5[0], c5[2], l5[1], l5[0], l5[2]);
+        const float dy = gauss3f(c5[3], c5[0], c5[4], l5[3], l5[0], l5[4]);
+        out.put(k, true, ky, kx, dx, dy);
     }
 }
 
@@ -772,8 +930,11 @@ static __device__ __forceinline__ void invalid_tile(const PassArgs &a, const Til
 
 // GC > 0: a kernel specialised for blocks of GC pixels, windows of 2 GC and
 // steps of GC (50 % overlap), so that window, step and block loops unroll.
+// FP32 kernels up to r = 4 are bounded to five CTAs per SM (48 registers),
+// except the 64 px windows, whose tiles are planned for three.
 template <int RC, int PREC, int GC>
-__global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 && RC <= 4)) ? 5 : 3) pass_kernel(const PassArgs a)
+__global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 && RC <= 4) && GC != 32) ? 5 : 3)
+    pass_kernel(const PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const PassPlan &P = a.plan;
@@ -850,10 +1011,14 @@ __global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 &
         block_planes_tc<(RC >= 0 ? RC : 0), PREC>(a, g, TA, TB, Ps);
     }
     __syncthreads();
+    if (PREC != PREC_FP32 && P.RGx > 1) {
+        reduce_row_groups(a, g, Ps);
+        __syncthreads();
+    }
 
     // 4: plane, argmax, FP32 stencil, Gaussian fit, outputs
     constexpr bool tc = PREC != PREC_FP32;
-    plane_and_peak<RC>(a, g, Ps, Vs, stats, tc, ws);
+    plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws);
     __syncthreads();
     stencil_direct(a, g, As, Bs, ws);
     __syncthreads();

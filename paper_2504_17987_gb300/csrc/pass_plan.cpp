@@ -102,13 +102,11 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     p.h_pitch = BC | 1;
     p.v_pitch = (BC - w + 1) | 1;
     if (prec == PREC_FP32) {
-        // partial planes per block: enough (block, sy, row-group) items to fill the CTA
+        // row groups per block: enough (block, sy, row-group) items to fill the
+        // CTA; a power of two dividing G, so that a group's partial planes sit
+        // in aligned lanes of one warp and are summed by shuffles
         int RG = 1;
-        while (RG < G && nb * ND * RG < plane_items()) {
-            int nx = RG + 1;
-            while (nx < G && G % nx) ++nx;
-            RG = nx;
-        }
+        while (2 * RG <= 32 && G % (2 * RG) == 0 && nb * ND * RG < plane_items()) RG *= 2;
         p.RGx = RG;
     } else {
         // warp per (block, row group): enough groups for the CTA's warps
@@ -137,7 +135,9 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     //   FP32: C (column box sums) -> P (block planes) + per-window stencil buffers
     //   TC:   C -> 16-bit copies TA, TB + P -> per-window buffers (over TA, TB) + P
     const int c_bytes = 2 * vh * p.h_pitch * 4;
-    const int p_bytes = up(nb * p.RGx * NP * 4, 16);
+    // FP32: one plane per block; TC: the row groups' partial planes, summed in place
+    p.pstride = (prec == PREC_FP32 ? 1 : p.RGx) * NP;
+    const int p_bytes = up(nb * p.pstride * 4, 16);
     const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(nwin * ngr * 5 * 4, 16);
     p.off_h = off;
     int region = 0, win_off = 0;
@@ -217,9 +217,11 @@ int min_ctas(int w, int prec)
 bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
 {
     // registers per thread as the kernels are built: the FP32 kernel is bounded
-    // to five CTAs per SM up to r = 4 (48 registers), three beyond; the
-    // tensor-core kernel to three
-    const int regs = (prec == PREC_FP32 && R <= 4) ? 48 : 80;
+    // to five CTAs per SM up to r = 4 (48 registers), three beyond and for the
+    // kernel specialised to 64 px windows at 50 % overlap; the tensor-core
+    // kernel to three
+    const bool wide = w == 64 && s == 32 && (R == 1 || R == 4);
+    const int regs = (prec == PREC_FP32 && R <= 4 && !wide) ? 48 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     const int override_kb = smem_budget_override();
     const int target = min_ctas(w, prec);

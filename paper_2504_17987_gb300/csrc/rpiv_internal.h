@@ -66,13 +66,14 @@ struct PassPlan {
     // tiling
     int TX, TY, tiles_x, tiles_y, threads;
     int G;    // block size of the block-decomposed correlation (= gcd(w, s))
-    int RGx;  // partial planes per block
+    int RGx;      // row groups per block in the plane phase
+    int pstride;  // floats between consecutive blocks' planes
     // shared-memory layout (byte offsets) for a full tile
     int smem_bytes;
     int off_a, a_pitch;          // A region, floats
     int off_b, b_pitch, padl;    // B' region, floats; logical column 0 at padl - (R+1)
     int off_h, h_pitch;          // C1 then C2 (column box sums), floats; odd pitch >= BC
-    int off_v, v_pitch;          // V1 then V2 (window box sums), floats; odd pitch >= hw
+    int off_v, v_pitch;          // V1 (window box sums of B') then VN (1 / sqrt of the box energy), floats; odd pitch >= hw
     int off_p;                   // block partial planes (aliases H)
     int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
     int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path; aliases H), elements

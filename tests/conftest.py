@@ -4,6 +4,9 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+# library workspaces, stage scratch and stage outputs start as NaN bytes in
+# the tests, so that a read of anything no kernel wrote cannot pass unnoticed
+os.environ.setdefault("RPIV_POISON_SCRATCH", "1")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
