@@ -183,26 +183,86 @@ static __device__ __forceinline__ bool load_regions(const PassArgs &a, const Til
     return true;
 }
 
-// 16-bit copies for the tensor-core path: A, and B' twice (the second shifted
-// one column left so that every column pair starts 4-byte aligned), with zeros
-// wherever fragments may reach outside the staged region.
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    if (PREC == PREC_BF16) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&v);
+    }
+    const __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// Rows of the A slab layout of the tensor-core path: slab j (block row
+// j / RG, row group j % RG) holds A rows j rows .. j rows + rows - 1 from TA
+// row tc_slab_row(j); the 2R rows before each slab and after the last are
+// zero, so that an MMA fragment of a used shift that reaches past its group
+// reads zeros; tc_front() leading rows keep the fragments of unused shifts
+// inside the array.
+__device__ __forceinline__ int tc_front(int R) { return max(0, 8 * ((2 * R + 8) / 8) - 1 - 2 * R); }
+__device__ __forceinline__ int tc_slab_row(int R, int rows, int j) { return tc_front(R) + 2 * R + j * (rows + 2 * R); }
+
+// 16-bit copies for the tensor-core path, two columns per conversion: A in
+// the slab layout, and B' twice, the second shifted one column left (TB1[x] =
+// B'[x + 1]) so that every column pair of a fragment starts 4-byte aligned,
+// with zeros wherever fragments reach outside the staged region.  A thread
+// keeps one column pair and walks rows.
 template <int PREC>
 __device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, uint16_t *TA,
                           uint16_t *TB)
 {
     const PassPlan &P = a.plan;
-    const int tid = threadIdx.x;
-    for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next())
-        TA[it.y * P.tca_pitch + it.x] = to_h16<PREC>(As[it.y * P.a_pitch + it.x]);
-    uint16_t *TB1 = TB + P.tb_rows * P.tcb_pitch;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int R = g.R, RG = P.RGx, rows = g.G / RG, stride = rows + 2 * R;
+    const int front = tc_front(R), nslab = g.nby * RG;
+    const int ta_rows = front + 2 * R + nslab * stride;
+    const int apairs = g.aw >> 1;  // aw is even (G even)
+    const int hpa = P.tca_pitch >> 1, lead = front + 2 * R;
+    for (int c0 = 0; c0 < apairs; c0 += nt) {
+        const int cols = min(apairs - c0, nt), step = nt / cols;
+        const int x2 = c0 + tid % cols, ph = tid / cols;
+        if (ph >= step) continue;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(TA) + x2;
+        const float *src = As + 2 * x2;
+        for (int row = ph; row < lead; row += step) dst[row * hpa] = 0u;
+        // slab rows: u = j stride + r, walked with (j, r) counters
+        int j = ph / stride, r = ph - (ph / stride) * stride;
+        for (int u = ph; u < ta_rows - lead; u += step) {
+            uint32_t v = 0u;
+            if (r < rows) {
+                const float2 f = *reinterpret_cast<const float2 *>(src + (j * rows + r) * P.a_pitch);
+                v = pack2<PREC>(f.x, f.y);
+            }
+            dst[(lead + u) * hpa] = v;
+            r += step;
+            while (r >= stride) {
+                r -= stride;
+                ++j;
+            }
+        }
+    }
+    uint32_t *TB1 = reinterpret_cast<uint32_t *>(TB + P.tb_rows * P.tcb_pitch);
+    uint32_t *TB0 = reinterpret_cast<uint32_t *>(TB);
     const int lo = g.OFFB, hi = g.OFFB + g.BC;  // staged columns
-    const int cols = P.tb_cols;                  // fragments of unused shifts reach past the region: zeros
-    for (Walk2D it(tid, blockDim.x, cols); it.y < g.BR; it.next()) {
-        const int y = it.y, x = it.x;
-        const float v0 = (x >= lo && x < hi) ? Bs[y * P.b_pitch + x] : 0.f;
-        const float v1 = (x + 1 >= lo && x + 1 < hi) ? Bs[y * P.b_pitch + x + 1] : 0.f;
-        TB[y * P.tcb_pitch + x] = to_h16<PREC>(v0);
-        TB1[y * P.tcb_pitch + x] = to_h16<PREC>(v1);
+    const int bpairs = P.tb_cols >> 1;           // fragments of unused shifts reach past the region: zeros
+    for (int c0 = 0; c0 < bpairs; c0 += nt) {
+        const int cols = min(bpairs - c0, nt), step = nt / cols;
+        const int x2 = c0 + tid % cols, ph = tid / cols;
+        if (ph >= step) continue;
+        const int x = 2 * x2;
+        const bool k0 = x >= lo && x < hi, k1 = x + 1 >= lo && x + 1 < hi, k2 = x + 2 >= lo && x + 2 < hi;
+        const int hpb = P.tcb_pitch >> 1;
+        const float *br = Bs + ph * P.b_pitch + x;
+        uint32_t *d0 = TB0 + ph * hpb + x2, *d1 = TB1 + ph * hpb + x2;
+        for (int y = ph; y < g.BR; y += step) {
+            const float v0 = k0 ? br[0] : 0.f, v1 = k1 ? br[1] : 0.f, v2 = k2 ? br[2] : 0.f;
+            *d0 = pack2<PREC>(v0, v1);
+            *d1 = pack2<PREC>(v1, v2);
+            br += step * P.b_pitch;
+            d0 += step * hpb;
+            d1 += step * hpb;
+        }
     }
 }
 
@@ -520,13 +580,15 @@ __device__ __forceinline__ void mma_k16(float (&d)[4], uint32_t a0, uint32_t a1,
 __device__ __forceinline__ uint32_t ld_pair(const uint16_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
 // Block planes on the tensor cores, one warp per (block, row group).  For
-// every row r of B' the block meets, the MMA multiplies
+// every row r of B' the group meets, the MMA multiplies
 //     X_r[sx][k] = B'[r][x0 + k + sx]        (a Toeplitz matrix of the row: M = sx)
 // by  Y_r[k][sy] = A[r - sy][x0 + k]        (the A rows r - sy of the group: N = sy)
 // over the block's columns k, so D[sx][sy] accumulates
 //     sum_r sum_k A[r - sy][x0 + k] B'[r][x0 + k + sx] = P_b(sy, sx)
-// directly, for every shift, across the rows (A rows outside the group enter
-// as zeros).  16 x 8 tiles: MT tiles of sx, NT tiles of sy.
+// directly, for every shift, across the rows.  A rows outside the group come
+// from the zero bands of the slab layout, so every fragment is one load at an
+// offset that only the row step changes.  16 x 8 tiles: MT tiles of sx, NT
+// tiles of sy.
 template <int R, int PREC>
 __device__ __forceinline__ void block_planes_tc(const PassArgs &a, const TileGeom &g, const uint16_t *TA, const uint16_t *TB,
                                 float *Ps)
@@ -539,19 +601,27 @@ __device__ __forceinline__ void block_planes_tc(const PassArgs &a, const TileGeo
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
     const int G = g.G, RG = P.RGx, rows = G / RG;
-    const uint16_t *TB1 = TB + P.tb_rows * P.tcb_pitch;
+    const int ap = P.tca_pitch, bp = P.tcb_pitch;
+    const uint16_t *TB1 = TB + P.tb_rows * bp;
     // smem column of Toeplitz element (m, k) of m-tile mt at block column X:
     //     padl - R + X + 16 mt + m + k;  X is even, so its parity is that of padl - R + m
     const int colbase = P.padl - R + gq + 2 * tq;
     // odd columns read the copy shifted by one (TB1[x] = B'[x + 1]) at x - 1
     const uint16_t *srcB = (colbase & 1) ? (TB1 - 1) : TB;
-    const bool k16 = (G % 16) == 0;
+    const int trips = rows + 2 * R;  // B' rows a group meets
     const int items = g.nb * RG;
     for (int it = warp; it < items; it += nwarps) {
         const int b = it / RG, gi = it - b * RG;
-        const int bxi = b % g.nbx, byi = b / g.nbx;
+        const int byi = b / g.nbx, bxi = b - byi * g.nbx;
         const int X0 = bxi * G;
-        const int i_lo = byi * G + gi * rows, i_hi = i_lo + rows;  // A rows of the group
+        const int i_lo = byi * G + gi * rows;  // first A row of the group
+        // step t: B' smem row i_lo + 1 + t; lane (n, gq) reads A row i_lo + t - 8 n - gq,
+        // i.e. slab row t - 8 n - gq
+        const uint16_t *pb = srcB + (i_lo + 1) * bp + colbase + X0;
+        const uint16_t *pa[NT];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) pa[n] = TA + (tc_slab_row(R, rows, byi * RG + gi) - 8 * n - gq) * ap + X0 + 2 * tq;
+        // the row step advances every fragment pointer by one row
         float acc[MT][NT][4];
 #pragma unroll
         for (int m = 0; m < MT; ++m)
@@ -559,48 +629,51 @@ __device__ __forceinline__ void block_planes_tc(const PassArgs &a, const TileGeo
             for (int n = 0; n < NT; ++n)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[m][n][e] = 0.f;
-        // smem rows of B': A row i at shift sy meets smem row i + sy + R + 1
-        for (int br = i_lo + 1; br <= i_hi - 1 + 2 * R + 1; ++br) {
-            const uint16_t *brow = srcB + br * P.tcb_pitch;
-            // A row of this lane's sy column n = gq in n-tile nt: i = br - 1 - 8 nt - gq
-            const uint16_t *arow[NT];
-            bool aok[NT];
+        if ((G % 16) == 0) {
+#pragma unroll 2
+            for (int t = 0; t < trips; ++t) {
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int i = br - 1 - 8 * n - gq;
-                aok[n] = i >= i_lo && i < i_hi;
-                arow[n] = TA + (aok[n] ? i : i_lo) * P.tca_pitch + 2 * tq;
-            }
-            if (k16) {
-                for (int X = X0; X < X0 + G; X += 16) {
+                for (int X = 0; X < G; X += 16) {
                     uint32_t bf[NT][2];
 #pragma unroll
                     for (int n = 0; n < NT; ++n) {
-                        bf[n][0] = aok[n] ? ld_pair(arow[n] + X) : 0u;
-                        bf[n][1] = aok[n] ? ld_pair(arow[n] + X + 8) : 0u;
+                        bf[n][0] = ld_pair(pa[n] + X);
+                        bf[n][1] = ld_pair(pa[n] + X + 8);
                     }
 #pragma unroll
                     for (int m = 0; m < MT; ++m) {
-                        const uint16_t *c = brow + colbase + X + 16 * m;
+                        const uint16_t *c = pb + X + 16 * m;
                         const uint32_t a0 = ld_pair(c), a1 = ld_pair(c + 8), a3 = ld_pair(c + 16);
 #pragma unroll
                         for (int n = 0; n < NT; ++n) mma_k16<PREC>(acc[m][n], a0, a1, a1, a3, bf[n][0], bf[n][1]);
                     }
                 }
-            } else {
-                for (int X = X0; X < X0 + G; X += 8) {
-                    const bool cok = (X - X0) + 2 * tq < G;  // columns past an uneven block enter as zeros
+#pragma unroll
+                for (int n = 0; n < NT; ++n) pa[n] += ap;
+                pb += bp;
+            }
+        } else {
+            // G = 8 (or another even size below 16): k8 steps; columns past
+            // the block (uneven G) enter as zeros
+#pragma unroll 4
+            for (int t = 0; t < trips; ++t) {
+#pragma unroll
+                for (int X = 0; X < G; X += 8) {
+                    const bool cok = (G % 8) == 0 || X + 2 * tq < G;
                     uint32_t bf[NT];
 #pragma unroll
-                    for (int n = 0; n < NT; ++n) bf[n] = (aok[n] && cok) ? ld_pair(arow[n] + X) : 0u;
+                    for (int n = 0; n < NT; ++n) bf[n] = cok ? ld_pair(pa[n] + X) : 0u;
 #pragma unroll
                     for (int m = 0; m < MT; ++m) {
-                        const uint16_t *c = brow + colbase + X + 16 * m;
+                        const uint16_t *c = pb + X + 16 * m;
                         const uint32_t a0 = ld_pair(c), a1 = ld_pair(c + 8);
 #pragma unroll
                         for (int n = 0; n < NT; ++n) mma_k8<PREC>(acc[m][n], a0, a1, bf[n]);
                     }
                 }
+#pragma unroll
+                for (int n = 0; n < NT; ++n) pa[n] += ap;
+                pb += bp;
             }
         }
         // D[m][n] of tile (mt, nt) is P_b(sy = 8 nt + n - R, sx = 16 mt + m - R)
@@ -722,7 +795,7 @@ struct WinShared {
     float *c5;    // [nwin][5] stencil values (plane-supplied ones), scaled by sqrt(E_A)
     int *peaks;   // [nwin] plane index of the argmax
     int *need;    // [nwin] bit p set: stencil point p needs a direct FP32 sum
-    float *dpart; // [nwin][ngr][5] direct numerators per 8-row group
+    float *dpart; // [nwin][ng][5] direct numerators per row group
 };
 
 // One warp per window: scaled plane from the block planes and box sums, argmax
@@ -823,43 +896,63 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
     }
 }
 
+// Row groups per window in the direct stencil: enough (window, group) items
+// for the CTA's warps when a tile has fewer windows than warps.
+__device__ __forceinline__ int stencil_groups(int nwin, int w, int nwarps) { return min(max(1, nwarps / nwin), w); }
+
 // Direct FP32 numerators of the stencil points the plane cannot supply: one
-// warp per (window, 8-row group), lanes along the columns, five accumulators.
+// warp per (window, row group), lanes over the group's pixels, five
+// accumulators; dpart[(wi ng + gr) 5 + p] holds a group's partial sum.
 static __device__ __forceinline__ void stencil_direct(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs,
                                       const WinShared &ws)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int w = g.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
-    for (int it = warp; it < g.nwin * ngr; it += nwarps) {
-        const int wi = it / ngr, gr = it - wi * ngr;
+    const int w = g.w, R = g.R, ND = g.ND;
+    const int ng = stencil_groups(g.nwin, w, nwarps);
+    const int bpt = P.b_pitch;
+    for (int it = warp; it < g.nwin * ng; it += nwarps) {
+        const int wi = it / ng, gr = it - wi * ng;
         const int need = ws.need[wi];
         if (!need) continue;
         const int q = ws.peaks[wi];
         const int ky = q / ND - R, kx = q % ND - R;
-        const int wxi = wi % g.nwx, wyi = wi / g.nwx;
-        const int rows = min(8, w - 8 * gr);
-        const float *abase = As + (wyi * g.s + 8 * gr) * P.a_pitch + wxi * g.s;
+        const int wyi = wi / g.nwx, wxi = wi - wyi * g.nwx;
+        const int r0 = gr * w / ng, r1 = (gr + 1) * w / ng;
+        const float *abase = As + (wyi * g.s + r0) * P.a_pitch + wxi * g.s;
         // B' at A pixel (r, x) and shift (sy, sx): row r + sy + R + 1, column x + sx + padl
-        const float *bbase = Bs + (wyi * g.s + 8 * gr + ky + R + 1) * P.b_pitch + P.padl + wxi * g.s + kx;
+        const float *bbase = Bs + (wyi * g.s + r0 + ky + R + 1) * bpt + P.padl + wxi * g.s + kx;
         float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        for (Walk2D e(lane, 32, w); e.y < rows; e.next()) {
-            const float av = abase[e.y * P.a_pitch + e.x];
-            const float *bb = bbase + e.y * P.b_pitch + e.x;
-            if (need & 1) acc[0] = fmaf(av, bb[0], acc[0]);
-            if (need & 2) acc[1] = fmaf(av, bb[-1], acc[1]);
-            if (need & 4) acc[2] = fmaf(av, bb[1], acc[2]);
-            if (need & 8) acc[3] = fmaf(av, bb[-P.b_pitch], acc[3]);
-            if (need & 16) acc[4] = fmaf(av, bb[P.b_pitch], acc[4]);
+        if (need == 0x1f) {
+            for (Walk2D e(lane, 32, w); e.y < r1 - r0; e.next()) {
+                const float av = abase[e.y * P.a_pitch + e.x];
+                const float *bb = bbase + e.y * bpt + e.x;
+                acc[0] = fmaf(av, bb[0], acc[0]);
+                acc[1] = fmaf(av, bb[-1], acc[1]);
+                acc[2] = fmaf(av, bb[1], acc[2]);
+                acc[3] = fmaf(av, bb[-bpt], acc[3]);
+                acc[4] = fmaf(av, bb[bpt], acc[4]);
+            }
+        } else {
+            for (Walk2D e(lane, 32, w); e.y < r1 - r0; e.next()) {
+                const float av = abase[e.y * P.a_pitch + e.x];
+                const float *bb = bbase + e.y * bpt + e.x;
+                if (need & 1) acc[0] = fmaf(av, bb[0], acc[0]);
+                if (need & 2) acc[1] = fmaf(av, bb[-1], acc[1]);
+                if (need & 4) acc[2] = fmaf(av, bb[1], acc[2]);
+                if (need & 8) acc[3] = fmaf(av, bb[-bpt], acc[3]);
+                if (need & 16) acc[4] = fmaf(av, bb[bpt], acc[4]);
+            }
         }
 #pragma unroll
-        for (int p = 0; p < 5; ++p) acc[p] = warp_sum(acc[p]);
+        for (int p = 0; p < 5; ++p)
+            if (need & (1 << p)) acc[p] = warp_sum(acc[p]);
         if (lane < 5) {
             float v = acc[0];
 #pragma unroll
             for (int p = 1; p < 5; ++p)
                 if (lane == p) v = acc[p];
-            ws.dpart[(wi * ngr + gr) * 5 + lane] = v;
+            ws.dpart[it * 5 + lane] = v;
         }
     }
 }
@@ -869,7 +962,8 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
                                 const WinShared &ws, int pair)
 {
     const PassPlan &P = a.plan;
-    const int w = g.w, R = g.R, ND = g.ND, ngr = (w + 7) / 8;
+    const int w = g.w, R = g.R, ND = g.ND;
+    const int ng = stencil_groups(g.nwin, w, blockDim.x >> 5);
     const int cp = P.v_pitch;
     const float *V1 = Vs, *VN = Vs + g.vh * cp;
     const WinOut out = win_out(a, pair);
@@ -893,7 +987,7 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
                 int sy, sx;
                 stencil_shift(p, ky, kx, sy, sx);
                 float num = 0.f;
-                for (int gr = 0; gr < ngr; ++gr) num += ws.dpart[(wi * ngr + gr) * 5 + p];
+                for (int gr = 0; gr < ng; ++gr) num += ws.dpart[(wi * ng + gr) * 5 + p];
                 const int vo = (wyi * g.s + R + 1 + sy) * cp + wxi * g.s + R + 1 + sx;
                 c = scaled_zncc(num, muA, V1[vo], VN[vo]);
             } else {

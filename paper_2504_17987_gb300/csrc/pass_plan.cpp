@@ -85,7 +85,7 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     const int BC = aw + 2 * (R + 1), BR = ah + 2 * (R + 1);
     const int vh = BR - w + 1;
     const int nb = (aw / G) * (ah / G);
-    const int nwin = TX * TY, ngr = (w + 7) / 8;
+    const int nwin = TX * TY;
     p.TX = TX;
     p.TY = TY;
     p.G = G;
@@ -109,14 +109,10 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
         while (2 * RG <= 32 && G % (2 * RG) == 0 && nb * ND * RG < plane_items()) RG *= 2;
         p.RGx = RG;
     } else {
-        // warp per (block, row group): enough groups for the CTA's warps
+        // warp per (block, row group): enough groups for the CTA's warps; a
+        // power of two dividing G, groups of at least two rows
         int RG = 1;
-        while (nb * RG < kThreads / 32) {
-            int nx = RG + 1;
-            while (nx < G && G % nx) ++nx;
-            if (nx > G || G / nx < 2) break;
-            RG = nx;
-        }
+        while (nb * RG < kThreads / 32 && G % (2 * RG) == 0 && G / (2 * RG) >= 2) RG *= 2;
         p.RGx = RG;
     }
     int off = 0;
@@ -138,7 +134,8 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     // FP32: one plane per block; TC: the row groups' partial planes, summed in place
     p.pstride = (prec == PREC_FP32 ? 1 : p.RGx) * NP;
     const int p_bytes = up(nb * p.pstride * 4, 16);
-    const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(nwin * ngr * 5 * 4, 16);
+    // direct stencil partials: (window, row group) items, at most max(nwin, warps)
+    const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(std::max(nwin, kThreads / 32) * 5 * 4, 16);
     p.off_h = off;
     int region = 0, win_off = 0;
     if (prec == PREC_FP32) {
@@ -153,7 +150,12 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
         p.tb_cols = up(p.padl - R + aw + 16 * MT + 8, 2);
         p.tca_pitch = odd8(aw);
         p.tcb_pitch = odd8(p.tb_cols);
-        const int ta_bytes = up(ah * p.tca_pitch * 2, 16);
+        // A in slabs per (block row, row group), 2R zero rows between them and
+        // around, after the leading rows that keep unused fragments in range
+        const int NT = (ND + 7) / 8, rows = G / p.RGx;
+        const int front = std::max(0, 8 * NT - 1 - 2 * R);
+        const int ta_rows = front + 2 * R + (ah / G) * p.RGx * (rows + 2 * R);
+        const int ta_bytes = up(ta_rows * p.tca_pitch * 2, 16);
         const int tb_bytes = up(2 * p.tb_rows * p.tcb_pitch * 2, 16);
         p.off_tca = off;
         p.off_tcb = off + ta_bytes;
@@ -191,13 +193,14 @@ bool pass_supported(int R, int prec)
     return false;
 }
 
-// CTAs per SM a tile must leave room for.  Swept on GB300 at 16 MP per pass
-// (targets 2..5): FP32 windows of 48 px and more run best at three CTAs,
-// whose larger tiles let neighbouring windows share their blocks (64 px:
-// 0.78 -> 0.59 ms), 24..40 px at four, smaller windows at five; the
-// tensor-core kernel, with its 16-bit copies, at three.  RPIV_MIN_CTAS
-// overrides it (tuning).
-int min_ctas(int w, int prec)
+// CTAs per SM a tile must leave room for.  Swept on GB300 (targets 2..6):
+// FP32 windows of 48 px and more run best at three CTAs, whose larger tiles
+// let neighbouring windows share their blocks (64 px: 0.78 -> 0.59 ms at
+// 16 MP), 24..40 px at four; below 24 px three at r >= 4 (16 px, r = 4:
+// 1.235 -> 1.192 ms per 64 MP launch) and five at small radii (16 px, r = 1:
+// 0.80 -> 0.69 ms); the tensor-core kernel, with its 16-bit copies, at three.
+// RPIV_MIN_CTAS overrides it (tuning).
+int min_ctas(int w, int R, int prec)
 {
     static int n = [] {
         const char *e = std::getenv("RPIV_MIN_CTAS");
@@ -206,7 +209,9 @@ int min_ctas(int w, int prec)
     }();
     if (n) return n;
     if (prec != PREC_FP32) return 3;
-    return w >= 48 ? 3 : (w >= 24 ? 4 : 5);
+    if (w >= 48) return 3;
+    if (w >= 24) return 4;
+    return R >= 4 ? 3 : 5;
 }
 
 // Tiles: among shapes of up to 8 x 8 windows (not necessarily square) that
@@ -224,7 +229,7 @@ bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan 
     const int regs = (prec == PREC_FP32 && R <= 4 && !wide) ? 48 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     const int override_kb = smem_budget_override();
-    const int target = min_ctas(w, prec);
+    const int target = min_ctas(w, R, prec);
     double best = -1e30;
     Layout pick{};
     int pick_tx = 0, pick_ty = 0;
