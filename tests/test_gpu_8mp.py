@@ -80,6 +80,10 @@ def test_full_size_pass_matches_oracle_on_sampled_windows(case, w, s, R, precisi
         assert (gap[disagree] <= 2e-5).all()
         err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
         assert err[m & same].max() <= TOL_PX
+        # FP32 rounding alone leaves the median near 2e-7 px; a bias in the
+        # deformation weights (e.g. a rounded reciprocal of a step that is not a
+        # power of two) shows up as about 2e-6
+        assert np.median(err[m & same]) <= 1e-6, f"median {np.median(err[m & same]):.3g} px"
     else:
         assert same[m].mean() >= 0.99, f"{precision} peak agreement {same[m].mean():.4f}"
         assert (gap[disagree] <= 0.02).all()
