@@ -90,7 +90,7 @@ struct StageDef {
     int prec;
     long long fpitch;  // floats per row of this stage's frames (margin layout)
     size_t off_pred, off_raw, off_info, off_out, off_mask;  // per-pair workspace offsets
-    PassPlan plan;
+    PassPlan plan, strip;
 };
 
 std::string check_config(const rpiv_config *c, std::vector<StageDef> *stages_out)
@@ -159,7 +159,7 @@ std::string check_config(const rpiv_config *c, std::vector<StageDef> *stages_out
             return "step " + std::to_string(d.s) + " is too small for the deformation kernel (minimum 3)";
         // a zero radius has a one-point plane: the FP32 kernel serves every precision
         d.prec = d.R == 0 ? PREC_FP32 : prec_of(c->precision);
-        if (!pass_plan(d.w, d.s, d.R, d.nx, d.ny, d.prec, &d.plan))
+        if (!pass_plan(d.w, d.s, d.R, d.nx, d.ny, d.prec, &d.plan, &d.strip))
             return "precision " + std::to_string((int)c->precision) + " is not built for radius " +
                    std::to_string(d.R) + " with window " + std::to_string(d.w) + " and step " + std::to_string(d.s);
     }
@@ -352,6 +352,7 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
         a.out_v = ws(d.off_raw + 4 * n1);
         a.out_info = ws(d.off_info);
         a.plan = d.plan;
+        a.strip = d.strip;
         TraceScope ts(h, st, "pass/" + stage_tag(h, d), geom_of(d.W, d.H, d.w, d.s, d.R, d.nx, d.ny, n));
         CK(launch_pass(a, n, st), "correlation pass launch");
         return RPIV_OK;
@@ -538,7 +539,7 @@ int rpiv::single_pass(const void *img_a, const void *img_b, size_t pitch_bytes, 
     PassArgs a;
     std::memset(&a, 0, sizeof(a));
     a.prec = radius == 0 ? PREC_FP32 : prec_of((rpiv_precision)precision);
-    if (!pass_plan(window, step, radius, nx, ny, a.prec, &a.plan))
+    if (!pass_plan(window, step, radius, nx, ny, a.prec, &a.plan, &a.strip))
         return fail(RPIV_ERR_UNSUPPORTED, "no kernel for this radius/precision/block size");
     const int M = frame_margin(radius);
     const long long fp = frame_pitch(width, M);

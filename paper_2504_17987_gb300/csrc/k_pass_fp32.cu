@@ -12,10 +12,23 @@ static cudaError_t go_fp32(const PassArgs &a, dim3 grid, int smem, cudaStream_t 
 
 // Specialised shapes: 50 % overlap with blocks of 8, 16 or 32 pixels (16, 32
 // and 64 px windows) at the radii of the benchmark schedules (1 and 4).
+template <int RC, int GC>
+static cudaError_t go_strip(const PassArgs &a, dim3 grid, int smem, cudaStream_t st)
+{
+    strip_kernel<RC, GC><<<grid, PASS_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int RC>
 static cudaError_t go_shaped(const PassArgs &a, dim3 grid, int smem, cudaStream_t st)
 {
     const int G = a.plan.G;
+    if (a.plan.strip_rows > 0) {
+        // strips are planned only for these shapes
+        if (G == 16) return go_strip<RC, 16>(a, grid, smem, st);
+        if (G == 32) return go_strip<RC, 32>(a, grid, smem, st);
+        return cudaErrorInvalidValue;
+    }
     if (a.w == 2 * G && a.s == G) {
         if (G == 8) return go_fp32<RC, 8>(a, grid, smem, st);
         if (G == 16) return go_fp32<RC, 16>(a, grid, smem, st);
@@ -64,6 +77,10 @@ void prepare_pass_fp32()
     set_smem(pass_kernel<4, PREC_FP32, 8>);
     set_smem(pass_kernel<4, PREC_FP32, 16>);
     set_smem(pass_kernel<4, PREC_FP32, 32>);
+    set_smem(strip_kernel<1, 16>);
+    set_smem(strip_kernel<1, 32>);
+    set_smem(strip_kernel<4, 16>);
+    set_smem(strip_kernel<4, 32>);
     cudaGetLastError();
 }
 

@@ -138,9 +138,10 @@ __device__ __forceinline__ int up4(int x) { return (x + 3) & ~3; }
 // from the float frames in the workspace (margin layout).  With a step that is
 // a multiple of 4 every row is one 16-byte-aligned bulk copy completing on an
 // mbarrier (bounded wait: on timeout the error word is set and false returned);
-// otherwise plain loads.
+// otherwise plain loads.  step: the CTA's k-th load (strips load once per
+// window row): the barrier is initialised at k = 0 and phase k completes it.
 static __device__ __forceinline__ bool load_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs,
-                                    uint64_t *bar)
+                                    uint64_t *bar, int step = 0)
 {
     const PassPlan &P = a.plan;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -158,8 +159,10 @@ static __device__ __forceinline__ bool load_regions(const PassArgs &a, const Til
         // warps wait at the caller's CTA barrier, which also makes the staged
         // rows visible to them, and leave the issue slots to co-resident CTAs
         if (tid >= 32) return true;
+        // the async copies follow the previous step's ordinary reads of the
+        // same rows (ordered by the caller's CTA barrier)
         if (lane == 0) {
-            mbar_init(bar, 1);
+            if (step == 0) mbar_init(bar, 1);
             fence_proxy_async();
         }
         __syncwarp();
@@ -167,12 +170,13 @@ static __device__ __forceinline__ bool load_regions(const PassArgs &a, const Til
         __syncwarp();
         for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
         for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
+        const uint32_t parity = (uint32_t)step & 1u;
         for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
-            if (mbar_try_wait(bar, 0)) return true;
+            if (mbar_try_wait(bar, parity)) return true;
         if (lane == 0 && a.err) atomicOr(a.err, 1);
         // give copies still in flight a bounded chance to land before the CTA exits
         for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
-            if (mbar_try_wait(bar, 0)) break;
+            if (mbar_try_wait(bar, parity)) break;
         return false;
     }
     for (Walk2D it(tid, blockDim.x, g.aw); it.y < g.ah; it.next())
@@ -202,6 +206,46 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 // inside the array.
 __device__ __forceinline__ int tc_front(int R) { return max(0, 8 * ((2 * R + 8) / 8) - 1 - 2 * R); }
 __device__ __forceinline__ int tc_slab_row(int R, int rows, int j) { return tc_front(R) + 2 * R + j * (rows + 2 * R); }
+
+// Strip loads on the bulk path (steps that are multiples of 4): warp 0 issues
+// the copies of a step's regions without waiting, so that they overlap the end
+// of the previous step; step k completes phase k of the barrier.
+static __device__ __forceinline__ void issue_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs,
+                                     uint64_t *bar, int step)
+{
+    const PassPlan &P = a.plan;
+    const int lane = threadIdx.x & 31;
+    const float *asrc = (const float *)resolve(a.adef.base ? a.adef : a.afl, pair);
+    const float *bsrc = (const float *)resolve(a.bdef, pair);
+    const long long dp = a.def_pitch;
+    const int M = a.def_margin;
+    const float *a0 = asrc + (long long)(g.ay0 + M) * dp + (g.ax0 + M);
+    const float *b0 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 + M - P.padl);
+    const int acols = up4(g.aw), bcols = up4(g.OFFB + g.BC);
+    const uint32_t bytes = (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
+    if (lane == 0) {
+        if (step == 0) mbar_init(bar, 1);
+        fence_proxy_async();
+    }
+    __syncwarp();
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
+    for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
+}
+
+// Bounded wait for step k's copies (warp 0); false after the limit, with the
+// error word set once the copies in flight had their chance to land.
+static __device__ __forceinline__ bool wait_regions(const PassArgs &a, uint64_t *bar, int step)
+{
+    const uint32_t parity = (uint32_t)step & 1u;
+    for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    if ((threadIdx.x & 31) == 0 && a.err) atomicOr(a.err, 1);
+    for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) break;
+    return false;
+}
 
 // 16-bit copies for the tensor-core path, two columns per conversion: A in
 // the slab layout, and B' twice, the second shifted one column left (TB1[x] =
@@ -406,7 +450,7 @@ static __device__ __forceinline__ void block_stats(const PassArgs &a, const Tile
 // E = sum M2_b + n_b sum (mean_b - mean)^2, in a fixed order.
 static __device__ __forceinline__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *bst, float *stats)
 {
-    const PassPlan &P = a.plan;
+    (void)a;
     const int G = g.G, kb = g.w / G;
     const float nb = (float)(G * G), n = (float)(g.w * g.w);
     for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
@@ -447,22 +491,26 @@ __device__ __forceinline__ void sum_row_groups(float (&acc)[ND], int lrg)
 // Compile-time radius: each thread owns one (block, sy, row group) and keeps
 // the 2R+1 accumulators of its sx row in registers; rows are streamed from
 // shared memory four columns at a time with aligned 128-bit loads.
+// b0: first block (strips compute only the new block row after their first
+// step); ring_wy >= 0: strip mode, block row by of window row ring_wy goes to
+// ring row (ring_wy + by) & 1.
 template <int R>
-__device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, float *Ps)
+__device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, float *Ps,
+                                  int b0 = 0, int ring_wy = -1)
 {
     constexpr int ND = 2 * R + 1;
     constexpr int MIS = ((-R) % 4 + 4) % 4;
     constexpr int NQ = (4 + 2 * R + MIS + 3) / 4;
     const PassPlan &P = a.plan;
     const int G = g.G, RG = P.RGx, rows = G / RG, lrg = __ffs(RG) - 1;
-    const int units = g.nb * ND;  // (block, sy)
+    const int units = (g.nb - b0) * ND;  // (block, sy)
     const int lane = threadIdx.x & 31, gi = lane >> (5 - lrg), ul = lane & ((32 >> lrg) - 1);
     // warp-uniform trip count for the shuffles; lanes past the last unit
     // repeat it and store nothing
     for (int base = (threadIdx.x - lane) >> lrg; base < units; base += blockDim.x >> lrg) {
         const int u = min(base + ul, units - 1);
-        const int b = u / ND;
-        const int syi = u - b * ND;
+        const int b = b0 + u / ND;
+        const int syi = u - (b - b0) * ND;
         const int byi = b / g.nbx, bxi = b - byi * g.nbx;
         const int c0 = bxi * G, r0 = byi * G + gi * rows;
         float acc[ND];
@@ -492,7 +540,8 @@ __device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileG
         }
         sum_row_groups<ND>(acc, lrg);
         if (base + ul < units && gi == 0) {
-            float *out = Ps + b * P.pstride + syi * ND;
+            const int pb = ring_wy < 0 ? b : ((ring_wy + byi) & 1) * g.nbx + bxi;
+            float *out = Ps + pb * P.pstride + syi * ND;
 #pragma unroll
             for (int d = 0; d < ND; ++d) out[d] = acc[d];
         }
@@ -805,9 +854,11 @@ struct WinShared {
 // RC >= 0: compile-time radius; each lane decodes the shifts it owns
 // (q = lane + 32 j) once, into plane and box-sum offsets kept in registers.
 // ONE_PLANE: one plane per block (FP32 planes), so the block stride is NP.
+// ring_wy >= 0: strip mode, the window's block rows yy sit in ring rows
+// (ring_wy + yy) & 1.
 template <int RC, bool ONE_PLANE>
 static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
-                                      const float *stats, bool tc, const WinShared &ws)
+                                      const float *stats, bool tc, const WinShared &ws, int ring_wy = -1)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -833,8 +884,10 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
     }
     auto block_sum = [&](const float *pb, int q) {
         float num = 0.f;
-        for (int yy = 0; yy < kb; ++yy)
-            for (int xx = 0; xx < kb; ++xx) num += pb[yy * rs + xx * ps + q];
+        for (int yy = 0; yy < kb; ++yy) {
+            const int ro = ring_wy < 0 ? yy * rs : ((ring_wy + yy) & 1) * rs;
+            for (int xx = 0; xx < kb; ++xx) num += pb[ro + xx * ps + q];
+        }
         return num;
     };
     for (Walk2D wk(warp, nwarps, g.nwx); wk.y < g.nwy; wk.next()) {
@@ -847,7 +900,7 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
             }
             continue;
         }
-        const float *pb = Ps + (wyi * sg * g.nbx + wxi * sg) * ps;
+        const float *pb = Ps + ((ring_wy < 0 ? wyi * sg * g.nbx : 0) + wxi * sg) * ps;
         const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
         const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
         float best = 0.f;
@@ -1117,6 +1170,104 @@ __global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 &
     stencil_direct(a, g, As, Bs, ws);
     __syncthreads();
     finalize(a, g, Vs, stats, ws, pair);
+}
+
+// A strip: one CTA walks P.strip_rows window rows of a one-row tile of TX
+// windows (50 % overlap, blocks of GC px: a window is 2 x 2 blocks).  Each step
+// loads its regions (the rows it shares with the previous step come from L2),
+// recomputes the statistics and box sums, computes the planes of the block row
+// it adds (both block rows on its first step) into a two-row ring, and takes
+// the block row it shares with the previous window row from the ring.  The
+// next step's copies are issued once the regions are last read (after the
+// direct stencil), so that they overlap the fit.  GC is a multiple of 4: every
+// region row is one bulk copy.
+template <int RC, int GC>
+__global__ void __launch_bounds__(PASS_THREADS, 3) strip_kernel(const PassArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PassPlan &P = a.plan;
+    TileGeom g;
+    g.R = RC;
+    g.ND = 2 * RC + 1;
+    g.NP = g.ND * g.ND;
+    g.G = GC;
+    g.w = 2 * GC;
+    g.s = GC;
+    g.kb = 2;
+    const int pair = blockIdx.z;
+    const int s = g.s, w = g.w;
+    g.wx0 = blockIdx.x * P.TX;
+    g.nwx = min(P.TX, a.nx - g.wx0);
+    g.nwy = 1;
+    g.nwin = g.nwx;
+    g.aw = (g.nwx - 1) * s + w;
+    g.ah = w;
+    g.ax0 = g.wx0 * s;
+    g.BC = g.aw + 2 * (g.R + 1);
+    g.BR = g.ah + 2 * (g.R + 1);
+    g.OFFB = P.padl - (g.R + 1);
+    g.hw = g.BC - w + 1;
+    g.vh = g.BR - w + 1;
+    g.nbx = g.aw / g.G;
+    g.nby = 2;
+    g.nb = 2 * g.nbx;
+
+    float *As = reinterpret_cast<float *>(smem + P.off_a);
+    float *Bs = reinterpret_cast<float *>(smem + P.off_b);
+    float *Cs = reinterpret_cast<float *>(smem + P.off_h);
+    float *Vs = reinterpret_cast<float *>(smem + P.off_v);
+    float *Ps = reinterpret_cast<float *>(smem + P.off_p);
+    float *stats = reinterpret_cast<float *>(smem + P.off_stats);
+    float2 *bst = reinterpret_cast<float2 *>(smem + P.off_gst);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + P.off_red);
+    WinShared ws;
+    ws.c5 = reinterpret_cast<float *>(smem + P.off_c5);
+    ws.peaks = reinterpret_cast<int *>(smem + P.off_peaks);
+    ws.need = reinterpret_cast<int *>(smem + P.off_need);
+    ws.dpart = reinterpret_cast<float *>(smem + P.off_dpart);
+
+    const int wy_begin = blockIdx.y * P.strip_rows, wy_end = min(a.ny, wy_begin + P.strip_rows);
+    g.wy0 = wy_begin;
+    g.ay0 = wy_begin * s;
+    if (threadIdx.x < 32) issue_regions(a, g, pair, As, Bs, bar, 0);
+    for (int wy = wy_begin; wy < wy_end; ++wy) {
+        const int k = wy - wy_begin;
+        g.wy0 = wy;
+        g.ay0 = wy * s;
+        // 1: A and B' regions of this window row (issued the step before)
+        const bool loaded = threadIdx.x < 32 ? wait_regions(a, bar, k) : true;
+        if (__syncthreads_or(!loaded)) {
+            for (int r = wy; r < wy_end; ++r) {
+                g.wy0 = r;
+                invalid_tile(a, g, pair);
+            }
+            return;
+        }
+        // 2: statistics and box sums of the row
+        block_stats(a, g, As, bst);
+        box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
+        __syncthreads();
+        window_stats(a, g, bst, stats);
+        // 3: planes of the block row this step adds
+        block_planes_fp32<RC>(a, g, As, Bs, Ps, k == 0 ? 0 : g.nbx, wy);
+        __syncthreads();
+        // 4: plane, argmax, FP32 stencil, Gaussian fit, outputs
+        plane_and_peak<RC, true>(a, g, Ps, Vs, stats, false, ws, wy);
+        __syncthreads();
+        stencil_direct(a, g, As, Bs, ws);
+        __syncthreads();
+        // the regions are read no more in this step: the next step's copies go
+        // out now, behind the CTA barrier that ordered the reads
+        if (wy + 1 < wy_end && threadIdx.x < 32) {
+            TileGeom gn = g;
+            gn.wy0 = wy + 1;
+            gn.ay0 = (wy + 1) * s;
+            issue_regions(a, gn, pair, As, Bs, bar, k + 1);
+        }
+        finalize(a, g, Vs, stats, ws, pair);
+        // the next step overwrites the sums and the window buffers
+        __syncthreads();
+    }
 }
 
 }  // namespace rpiv

@@ -76,7 +76,9 @@ struct Layout {
     PassPlan p;
 };
 
-Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
+// strip: a one-row tile whose CTA walks window rows; its block planes live in
+// a two-row ring outside the reused region, since they outlive a step
+Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool strip = false)
 {
     PassPlan p;
     std::memset(&p, 0, sizeof(p));
@@ -127,6 +129,7 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     p.off_stats = take(2 * nwin * 4);
     p.off_red = take(16);      // the region loads' mbarrier
     p.off_gst = take(nb * 8);  // per-block (sum, centred sum of squares) of A
+    if (strip) p.off_p = take(2 * (aw / G) * NP * 4);
     // region reused over the phases:
     //   FP32: C (column box sums) -> P (block planes) + per-window stencil buffers
     //   TC:   C -> 16-bit copies TA, TB + P -> per-window buffers (over TA, TB) + P
@@ -138,7 +141,10 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec)
     const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(std::max(nwin, kThreads / 32) * 5 * 4, 16);
     p.off_h = off;
     int region = 0, win_off = 0;
-    if (prec == PREC_FP32) {
+    if (prec == PREC_FP32 && strip) {
+        win_off = off;
+        region = std::max(c_bytes, win_bytes);
+    } else if (prec == PREC_FP32) {
         p.off_p = off;
         win_off = off + p_bytes;
         region = std::max(c_bytes, p_bytes + win_bytes);
@@ -258,16 +264,80 @@ bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan 
     return true;
 }
 
-bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan)
+namespace {
+
+// Window rows a strip CTA walks (RPIV_STRIP_ROWS, tuning; 0 turns strips off).
+// The first row of a segment computes both block rows, the others one.
+int strip_rows_setting()
+{
+    static int n = [] {
+        const char *e = std::getenv("RPIV_STRIP_ROWS");
+        if (!e) return 8;
+        const int v = std::atoi(e);
+        return (v >= 0 && v <= 4096) ? v : 8;
+    }();
+    return n;
+}
+
+}  // namespace
+
+// Strips for the FP32 kernels specialised to 50 % overlap with 32 px blocks
+// (64 px windows) at r = 1 and 4: among one-row tiles of up to 8 windows that
+// leave room for three CTAs per SM, the widest.  (Measured: 64 px passes
+// 1.347 -> 1.169 ms per 64-pair launch; 32 px passes were no faster.)
+bool plan_strip(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
+{
+    const int L = strip_rows_setting();
+    if (prec != PREC_FP32 || L < 2 || ny < 2 || w != 2 * s || s != G || G != 32 || (R != 1 && R != 4))
+        return false;
+    const int regs = 80;  // the strip kernels are bounded to three CTAs per SM
+    const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
+    const int target = min_ctas(w, R, prec);
+    int pick_tx = 0;
+    Layout pick{};
+    for (int tx = 1; tx <= std::min(8, nx); ++tx) {
+        Layout Lo = layout_for(tx, 1, w, s, R, G, prec, true);
+        if (Lo.bytes > kSmemMax) continue;
+        const int ctas = std::min({228 * 1024 / (Lo.bytes + 1024), by_regs, by_threads});
+        if (ctas < std::min(target, 3)) continue;
+        pick_tx = tx;
+        pick = Lo;
+    }
+    if (pick_tx == 0) return false;
+    *plan = pick.p;
+    plan->strip_rows = std::min(L, ny);
+    plan->tiles_x = (nx + pick_tx - 1) / pick_tx;
+    plan->tiles_y = (ny + plan->strip_rows - 1) / plan->strip_rows;
+    return true;
+}
+
+bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan, PassPlan *strip)
 {
     if (w < 2 || s < 1 || nx < 1 || ny < 1 || !pass_supported(R, prec)) return false;
     const int G = gcd(w, s);
     if (prec != PREC_FP32 && (G % 2) != 0) return false;  // paired 16-bit loads need even blocks
+    if (strip) {
+        std::memset(strip, 0, sizeof(*strip));
+        if (!plan_strip(w, s, R, G, nx, ny, prec, strip)) std::memset(strip, 0, sizeof(*strip));
+    }
     return plan_search(w, s, R, G, nx, ny, prec, plan);
 }
 
-cudaError_t launch_pass(const PassArgs &args, int n_pairs, cudaStream_t st)
+// A strip launch walks its segments serially inside each CTA, so it is taken
+// only when the batch gives it about four waves of CTAs (three per SM).
+constexpr long long kStripMinCtas = 4LL * 152 * 3;
+
+cudaError_t launch_pass(const PassArgs &args_in, int n_pairs, cudaStream_t st)
 {
+    const PassArgs *pa = &args_in;
+    PassArgs strip_args;
+    if (args_in.strip.strip_rows > 0 &&
+        (long long)args_in.strip.tiles_x * args_in.strip.tiles_y * n_pairs >= kStripMinCtas) {
+        strip_args = args_in;
+        strip_args.plan = args_in.strip;
+        pa = &strip_args;
+    }
+    const PassArgs &args = *pa;
     dim3 grid(args.plan.tiles_x, args.plan.tiles_y, n_pairs);
     const int smem = args.plan.smem_bytes;
     switch (args.prec) {

@@ -66,6 +66,8 @@ struct PassPlan {
     // tiling
     int TX, TY, tiles_x, tiles_y, threads;
     int G;    // block size of the block-decomposed correlation (= gcd(w, s))
+    int strip_rows;  // > 0: each CTA walks this many window rows of a one-row tile, keeping
+                     // the previous block row's planes (tiles_y counts the strip segments)
     int RGx;      // row groups per block in the plane phase
     int pstride;  // floats between consecutive blocks' planes
     // shared-memory layout (byte offsets) for a full tile
@@ -74,7 +76,7 @@ struct PassPlan {
     int off_b, b_pitch, padl;    // B' region, floats; logical column 0 at padl - (R+1)
     int off_h, h_pitch;          // C1 then C2 (column box sums), floats; odd pitch >= BC
     int off_v, v_pitch;          // V1 (window box sums of B') then VN (1 / sqrt of the box energy), floats; odd pitch >= hw
-    int off_p;                   // block partial planes (aliases H)
+    int off_p;                   // block planes (aliases H; a two-row ring of its own in strips)
     int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
     int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path; aliases H), elements
     int tb_rows, tb_cols;        // rows of each B' copy, columns written
@@ -102,6 +104,8 @@ struct PassArgs {
     PtrRef out_u, out_v;   // raw field
     PtrRef out_info;       // int32: bit0 valid, bits 8..15 ky, 16..23 kx
     PassPlan plan;
+    PassPlan strip;        // strip alternative to the tile plan (strip_rows 0: none); the
+                           // launch takes it when the batch gives it enough CTAs
 };
 
 struct DeformArgs {
@@ -150,7 +154,9 @@ int single_pass(const void *img_a, const void *img_b, size_t pitch_bytes, int fm
                 int32_t *info, void *scratch, cudaStream_t st);
 
 // Returns false if (w, s, R, prec) is not supported by a compiled kernel.
-bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan);
+// Tile plan of a correlation pass; strip (nullable) receives the strip
+// alternative, strip_rows 0 when the shape has none.
+bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan, PassPlan *strip = nullptr);
 cudaError_t launch_pass(const PassArgs &args, int n_pairs, cudaStream_t st);
 bool pass_supported(int R, int prec);
 

@@ -111,7 +111,7 @@ def test_correlate_zero_predictor_plain_256():
 
 
 @pytest.mark.parametrize("w,s,R", [(64, 32, 4), (32, 16, 4), (16, 8, 4), (32, 8, 8), (48, 24, 6), (16, 8, 1),
-                                   (24, 12, 6), (16, 8, 0), (20, 10, 3), (16, 12, 2)])
+                                   (24, 12, 6), (16, 8, 0), (20, 10, 3), (16, 12, 2), (32, 16, 1), (64, 32, 1)])
 def test_correlate_with_predictor_fp32(w, s, R):
     wk = wl.paper_1mp(W=320, H=288)
     A, B = wk.render()
