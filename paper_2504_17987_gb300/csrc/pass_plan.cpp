@@ -281,25 +281,28 @@ int strip_rows_setting()
 
 }  // namespace
 
-// Strips for the FP32 kernels specialised to 50 % overlap with 32 px blocks
-// (64 px windows) at r = 1 and 4: among one-row tiles of up to 8 windows that
-// leave room for three CTAs per SM, the widest.  (Measured: 64 px passes
-// 1.347 -> 1.169 ms per 64-pair launch; 32 px passes were no faster.)
+// Strips for the FP32 kernels specialised to 50 % overlap with 16 or 32 px
+// blocks (32 and 64 px windows) at r = 1 and 4: among one-row tiles of up to
+// 8 windows that leave room for the kernel's CTAs per SM, the widest.
+// Measured per 64-pair launch of the 1 MP workload: 64 px passes 1.346 ->
+// 1.160 ms (three CTAs per SM), 32 px passes 1.083 -> 1.001 ms (four; at
+// three they were no faster).
 bool plan_strip(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
 {
     const int L = strip_rows_setting();
-    if (prec != PREC_FP32 || L < 2 || ny < 2 || w != 2 * s || s != G || G != 32 || (R != 1 && R != 4))
+    if (prec != PREC_FP32 || L < 2 || ny < 2 || w != 2 * s || s != G || (G != 16 && G != 32) || (R != 1 && R != 4))
         return false;
-    const int regs = 80;  // the strip kernels are bounded to three CTAs per SM
+    // the strip kernels are bounded to three CTAs per SM (80 registers), four for 16 px blocks
+    const int target = G == 16 ? 4 : 3;
+    const int regs = G == 16 ? 64 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
-    const int target = min_ctas(w, R, prec);
     int pick_tx = 0;
     Layout pick{};
     for (int tx = 1; tx <= std::min(8, nx); ++tx) {
         Layout Lo = layout_for(tx, 1, w, s, R, G, prec, true);
         if (Lo.bytes > kSmemMax) continue;
         const int ctas = std::min({228 * 1024 / (Lo.bytes + 1024), by_regs, by_threads});
-        if (ctas < std::min(target, 3)) continue;
+        if (ctas < target) continue;
         pick_tx = tx;
         pick = Lo;
     }
