@@ -20,9 +20,9 @@ namespace rpiv {
 
 namespace {
 
-constexpr int DTX = 64, DTY = 64;  // output pixels per CTA
-constexpr int DROWS = 8;           // rows per thread and 32-row slice (256 threads = 64 columns x 4 row phases)
-constexpr int NODE_CAP = 640;      // nodes a tile can touch (checked on the host)
+constexpr int DTX = 64, DTY = 128;  // output pixels per CTA
+constexpr int DROWS = 8;            // rows per thread and 32-row slice (256 threads = 64 columns x 4 row phases)
+constexpr int NODE_CAP = 1152;      // nodes a tile can touch (checked on the host; steps >= 3)
 constexpr int NROW_CAP = DTY / 3 + 4;  // node rows a tile touches (steps >= 3, checked on the host)
 
 // cell index and weight of a pixel position along one axis of the node grid

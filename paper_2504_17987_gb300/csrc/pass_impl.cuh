@@ -1182,7 +1182,7 @@ __global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 &
 // direct stencil), so that they overlap the fit.  GC is a multiple of 4: every
 // region row is one bulk copy.
 template <int RC, int GC>
-__global__ void __launch_bounds__(PASS_THREADS, GC == 16 ? 4 : 3) strip_kernel(const PassArgs a)
+__global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(const PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const PassPlan &P = a.plan;

@@ -286,15 +286,16 @@ int strip_rows_setting()
 // 8 windows that leave room for the kernel's CTAs per SM, the widest.
 // Measured per 64-pair launch of the 1 MP workload: 64 px passes 1.346 ->
 // 1.160 ms (three CTAs per SM), 32 px passes 1.083 -> 1.001 ms (four; at
-// three they were no faster).
+// three they were no faster).  16 px strips were slower (1.215 -> 1.789 ms):
+// with 8 px blocks the per-row box sums and barriers outweigh the planes saved.
 bool plan_strip(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
 {
     const int L = strip_rows_setting();
     if (prec != PREC_FP32 || L < 2 || ny < 2 || w != 2 * s || s != G || (G != 16 && G != 32) || (R != 1 && R != 4))
         return false;
     // the strip kernels are bounded to three CTAs per SM (80 registers), four for 16 px blocks
-    const int target = G == 16 ? 4 : 3;
-    const int regs = G == 16 ? 64 : 80;
+    const int target = G == 32 ? 3 : 4;
+    const int regs = G == 32 ? 80 : 64;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     int pick_tx = 0;
     Layout pick{};
