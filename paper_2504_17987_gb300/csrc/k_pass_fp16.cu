@@ -1,5 +1,5 @@
-// FP16 tensor-core (mma.sync m16n8k8, FP32 accumulate) instantiations of the
-// fused correlation pass.
+// FP16 tensor-core (mma.sync m16n8k16, k8 for 8 px blocks, FP32 accumulate)
+// instantiations of the fused correlation pass.
 #include "pass_impl.cuh"
 
 namespace rpiv {

@@ -4,8 +4,8 @@
 // is produced beforehand by the deformation kernel (k_deform.cu).
 //
 // Work of one CTA, staged in shared memory:
-//   A region   A - mu_T over the union of the tile's windows (aw x ah)
-//   B' region  B' - mu_T over the A region grown by R+1 on each side
+//   A region   raw A over the union of the tile's windows (aw x ah)
+//   B' region  raw B' over the A region grown by R+1 on each side
 //   C, V       sliding box sums of B' and B'^2 (C: columns, V: rows); V1[r][c]
 //              is the sum of B' over the w x w box with top-left logical B'
 //              pixel (r, c), VN[r][c] = 1 / sqrt(E_B) of that box (0 when the
@@ -20,11 +20,14 @@
 // per-window scale leaves the argmax unchanged; the five stencil values are
 // scaled back by 1 / sqrt(E_A) before the fit.
 // The planes are formed with FP32 FMAs on the CUDA cores, or with BF16/FP16
-// tensor-core MMAs (mma.sync m16n8k8, FP32 accumulate) whose accumulator tile
-// D[i][j] (i = B' row, j = A row of an 8-row sub-block) carries shift
-// sy = i - j - R on its diagonals.  The argmax is taken on the plane; the
-// 5-point stencil of the Gaussian fit is evaluated in FP32 (from the FP32
-// planes, or by direct sums on the tensor-core path and for shifts R+1).
+// tensor-core MMAs (mma.sync, FP32 accumulate) that multiply the Toeplitz
+// matrix of a B' row (rows: sx) by the A rows that meet it (columns: sy), so
+// that the accumulators hold P_b(sy, sx).  The 5-point stencil of the
+// Gaussian fit is evaluated in FP32 (from the FP32 planes, or by direct sums
+// on the tensor-core path and for shifts R+1).
+// Strips (strip_kernel): for 50 % overlap with 16 or 32 px blocks a CTA walks
+// the window rows of a one-row tile and keeps the block row two window rows
+// share, so each block row's planes are computed once per strip segment.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -1148,7 +1151,7 @@ __global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 &
         __syncthreads();
     }
 
-    // 3: block partial planes (alias the dead C region)
+    // 3: block planes (alias the dead C region)
     if (PREC == PREC_FP32) {
         if (RC >= 0)
             block_planes_fp32<(RC >= 0 ? RC : 0)>(a, g, As, Bs, Ps);

@@ -47,7 +47,8 @@ constexpr int kSmemMax = 227 * 1024;
 
 // (block, sy, row group) items the FP32 plane loop aims for before it stops
 // splitting blocks into row groups: half the CTA's threads (swept on GB300:
-// 64..512, 128 best; more groups cost more partial planes to sum).
+// 64..512, 128 best, again after row groups came to be summed by shuffles;
+// more groups cost more shuffles).
 // RPIV_PLANE_ITEMS overrides it (tuning).
 int plane_items()
 {
@@ -329,14 +330,26 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan, Pa
 
 // A strip launch walks its segments serially inside each CTA, so it is taken
 // only when the batch gives it about four waves of CTAs (three per SM).
+// RPIV_STRIP_MIN_CTAS overrides the threshold (tuning, and the tests that run
+// both forms); it is read at each launch.
 constexpr long long kStripMinCtas = 4LL * 152 * 3;
+
+long long strip_min_ctas()
+{
+    const char *e = std::getenv("RPIV_STRIP_MIN_CTAS");
+    if (e) {
+        const long long v = std::atoll(e);
+        if (v >= 1) return v;
+    }
+    return kStripMinCtas;
+}
 
 cudaError_t launch_pass(const PassArgs &args_in, int n_pairs, cudaStream_t st)
 {
     const PassArgs *pa = &args_in;
     PassArgs strip_args;
     if (args_in.strip.strip_rows > 0 &&
-        (long long)args_in.strip.tiles_x * args_in.strip.tiles_y * n_pairs >= kStripMinCtas) {
+        (long long)args_in.strip.tiles_x * args_in.strip.tiles_y * n_pairs >= strip_min_ctas()) {
         strip_args = args_in;
         strip_args.plan = args_in.strip;
         pa = &strip_args;

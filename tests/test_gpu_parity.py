@@ -110,9 +110,14 @@ def test_correlate_zero_predictor_plain_256():
     check_fp32_pass(r, 8)
 
 
+@pytest.mark.parametrize("form", ["tiles", "strips"])
 @pytest.mark.parametrize("w,s,R", [(64, 32, 4), (32, 16, 4), (16, 8, 4), (32, 8, 8), (48, 24, 6), (16, 8, 1),
                                    (24, 12, 6), (16, 8, 0), (20, 10, 3), (16, 12, 2), (32, 16, 1), (64, 32, 1)])
-def test_correlate_with_predictor_fp32(w, s, R):
+def test_correlate_with_predictor_fp32(w, s, R, form, monkeypatch):
+    # strips (32 and 64 px windows at 50 %, r = 1 and 4) are taken at launch
+    # only for large batches; the threshold is lowered here to run them on one
+    # pair, and raised to keep the tile kernels
+    monkeypatch.setenv("RPIV_STRIP_MIN_CTAS", "1" if form == "strips" else str(1 << 40))
     wk = wl.paper_1mp(W=320, H=288)
     A, B = wk.render()
     nx, ny = oracle.grid_n(320, w, s), oracle.grid_n(288, w, s)
