@@ -1081,9 +1081,11 @@ static __device__ __forceinline__ void invalid_tile(const PassArgs &a, const Til
 // GC > 0: a kernel specialised for blocks of GC pixels, windows of 2 GC and
 // steps of GC (50 % overlap), so that window, step and block loops unroll.
 // FP32 kernels up to r = 4 are bounded to five CTAs per SM (48 registers),
-// except the 64 px windows, whose tiles are planned for three.
+// except the 64 px windows and the 16 px windows at r = 4, whose tiles are
+// planned for three.
 template <int RC, int PREC, int GC>
-__global__ void __launch_bounds__(PASS_THREADS, (PREC == PREC_FP32 && (RC >= 0 && RC <= 4) && GC != 32) ? 5 : 3)
+__global__ void __launch_bounds__(PASS_THREADS,
+                                  (PREC == PREC_FP32 && (RC >= 0 && RC <= 4) && GC != 32 && !(GC == 8 && RC == 4)) ? 5 : 3)
     pass_kernel(const PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];

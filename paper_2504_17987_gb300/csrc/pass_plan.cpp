@@ -107,9 +107,11 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool str
     if (prec == PREC_FP32) {
         // row groups per block: enough (block, sy, row-group) items to fill the
         // CTA; a power of two dividing G, so that a group's partial planes sit
-        // in aligned lanes of one warp and are summed by shuffles
+        // in aligned lanes of one warp and are summed by shuffles.  A strip step
+        // computes one block row.
+        const int nb_step = strip ? aw / G : nb;
         int RG = 1;
-        while (2 * RG <= 32 && G % (2 * RG) == 0 && nb * ND * RG < plane_items()) RG *= 2;
+        while (2 * RG <= 32 && G % (2 * RG) == 0 && nb_step * ND * RG < plane_items()) RG *= 2;
         p.RGx = RG;
     } else {
         // warp per (block, row group): enough groups for the CTA's warps; a
@@ -232,7 +234,7 @@ bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan 
     // to five CTAs per SM up to r = 4 (48 registers), three beyond and for the
     // kernel specialised to 64 px windows at 50 % overlap; the tensor-core
     // kernel to three
-    const bool wide = w == 64 && s == 32 && (R == 1 || R == 4);
+    const bool wide = (w == 64 && s == 32 && (R == 1 || R == 4)) || (w == 16 && s == 8 && R == 4);
     const int regs = (prec == PREC_FP32 && R <= 4 && !wide) ? 48 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
     const int override_kb = smem_budget_override();
