@@ -952,6 +952,101 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
     }
 }
 
+// FP32 planes, compile-time radius: two windows per warp, one per half-warp
+// (window 2 pw + h for half h), 16 lanes over the shifts q = lane + 16 j, so
+// that the per-window set-up, reduction and stencil work is shared by two
+// windows.  The half's argmax is a butterfly over (order key, q): the largest
+// value, ties to the smallest row-major index, NaN never winning.  Results
+// as plane_and_peak.
+template <int RC>
+static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, const TileGeom &g, const float *Ps,
+                                            const float *Vs, const float *stats, const WinShared &ws,
+                                            int ring_wy = -1)
+{
+    constexpr int R = RC, ND = 2 * RC + 1, NP = ND * ND;
+    constexpr int NQ = (NP + 15) / 16;
+    constexpr uint32_t NONE = 0xffffffffu;
+    const PassPlan &P = a.plan;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int h = lane >> 4, hl = lane & 15;
+    const int kb = g.kb, sg = g.s / g.G;
+    const int ps = NP, rs = g.nbx * ps;
+    const float tau = TAU_PER_PIXEL * (float)(g.w * g.w);
+    const int cp = P.v_pitch;
+    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    int qv[NQ], vv[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const int q = min(hl + 16 * j, NP - 1);
+        const int qy = q / ND, qx = q - qy * ND;
+        qv[j] = q;
+        vv[j] = (qy - R) * cp + (qx - R);
+    }
+    auto block_sum = [&](const float *pb, int q) {
+        float num = 0.f;
+        for (int yy = 0; yy < kb; ++yy) {
+            const int ro = ring_wy < 0 ? yy * rs : ((ring_wy + yy) & 1) * rs;
+            for (int xx = 0; xx < kb; ++xx) num += pb[ro + xx * ps + q];
+        }
+        return num;
+    };
+    const int npairs = (g.nwin + 1) >> 1;
+    for (int pw = warp; pw < npairs; pw += nwarps) {
+        const int wi = 2 * pw + h;
+        const bool has = wi < g.nwin;  // the second half of an odd tile's last pair idles
+        const int wic = has ? wi : g.nwin - 1;
+        const int wyi = wic / g.nwx, wxi = wic - wyi * g.nwx;
+        const float muA = stats[2 * wic], EA = stats[2 * wic + 1];
+        const bool live = has && EA > tau;  // degenerate windows: finalize passes the predictor
+        const float *pb = Ps + ((ring_wy < 0 ? wyi * sg * g.nbx : 0) + wxi * sg) * ps;
+        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        float best = 0.f;
+        uint32_t bq = NONE;
+        if (live) {
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                if (j < NQ - 1 || hl + 16 * j < NP) {
+                    const float c = scaled_zncc(block_sum(pb, qv[j]), muA, v1[vv[j]], vn[vv[j]]);
+                    // ascending q: the first of equal values stays; NaN never wins
+                    if (c > best || (bq == NONE && c == c)) {
+                        best = c;
+                        bq = (uint32_t)qv[j];
+                    }
+                }
+            }
+        }
+        uint32_t key = bq == NONE ? 0u : ord_key(best), kq = bq;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(0xffffffffu, key, o), oq = __shfl_xor_sync(0xffffffffu, kq, o);
+            if (ok > key || (ok == key && oq < kq)) {
+                key = ok;
+                kq = oq;
+            }
+        }
+        const int bidx = kq < (uint32_t)NP ? (int)kq : NP / 2;  // no finite value: zero shift
+        const int ky = bidx / ND - R, kx = bidx % ND - R;
+        float c = 0.f;
+        bool direct = false;
+        if (hl < 5 && live) {
+            int sy, sx;
+            stencil_shift(hl, ky, kx, sy, sx);
+            direct = !(sy >= -R && sy <= R && sx >= -R && sx <= R);
+            if (!direct) {
+                const int q = (sy + R) * ND + (sx + R), vo = sy * cp + sx;
+                c = scaled_zncc(block_sum(pb, q), muA, v1[vo], vn[vo]);
+            }
+        }
+        const unsigned bits = (__ballot_sync(0xffffffffu, direct) >> (16 * h)) & 0x1fu;
+        if (has && hl < 5) ws.c5[wi * 5 + hl] = c;
+        if (has && hl == 0) {
+            ws.peaks[wi] = live ? bidx : NP / 2;
+            ws.need[wi] = live ? (int)bits : 0;
+        }
+    }
+}
+
 // Row groups per window in the direct stencil: enough (window, group) items
 // for the CTA's warps when a tile has fewer windows than warps.
 __device__ __forceinline__ int stencil_groups(int nwin, int w, int nwarps) { return min(max(1, nwarps / nwin), w); }
@@ -1170,7 +1265,13 @@ __global__ void __launch_bounds__(PASS_THREADS,
 
     // 4: plane, argmax, FP32 stencil, Gaussian fit, outputs
     constexpr bool tc = PREC != PREC_FP32;
-    plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws);
+    // two windows per warp once the tile has at least two per warp (16 px
+    // tiles: 1.207 -> 1.198 ms per 64-pair launch; with fewer windows the
+    // warps left idle cost more than the shared set-up saves)
+    if (PREC == PREC_FP32 && RC >= 0 && g.nwin >= 2 * (int)(blockDim.x >> 5))
+        plane_and_peak_pairs<(RC >= 0 ? RC : 0)>(a, g, Ps, Vs, stats, ws);
+    else
+        plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws);
     __syncthreads();
     stencil_direct(a, g, As, Bs, ws);
     __syncthreads();
