@@ -350,11 +350,21 @@ cudaError_t launch_pass(const PassArgs &args_in, int n_pairs, cudaStream_t st)
 {
     const PassArgs *pa = &args_in;
     PassArgs strip_args;
-    if (args_in.strip.strip_rows > 0 &&
-        (long long)args_in.strip.tiles_x * args_in.strip.tiles_y * n_pairs >= strip_min_ctas()) {
-        strip_args = args_in;
-        strip_args.plan = args_in.strip;
-        pa = &strip_args;
+    if (args_in.strip.strip_rows > 0) {
+        // the planned segment length, or shorter segments (down to 2 window
+        // rows) when those give the launch enough CTAs
+        const int ny = args_in.ny;
+        for (int L = args_in.strip.strip_rows; L >= 2; L /= 2) {
+            const long long segs = (ny + L - 1) / L;
+            if ((long long)args_in.strip.tiles_x * segs * n_pairs >= strip_min_ctas()) {
+                strip_args = args_in;
+                strip_args.plan = args_in.strip;
+                strip_args.plan.strip_rows = L;
+                strip_args.plan.tiles_y = (int)segs;
+                pa = &strip_args;
+                break;
+            }
+        }
     }
     const PassArgs &args = *pa;
     dim3 grid(args.plan.tiles_x, args.plan.tiles_y, n_pairs);
