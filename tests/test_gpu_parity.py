@@ -244,7 +244,10 @@ def test_pipeline_paper_1mp_end_to_end_stagewise():
     assert np.mean(m == ref.mask) >= 0.99
 
 
-def test_pipeline_supplied_predictor_and_batch_equals_single():
+@pytest.mark.parametrize("form", ["tiles", "strips"])
+def test_pipeline_supplied_predictor_and_batch_equals_single(form, monkeypatch):
+    # the engine's 64 and 32 px passes as tiles, and as strips (forced at any batch size)
+    monkeypatch.setenv("RPIV_STRIP_MIN_CTAS", "1" if form == "strips" else str(1 << 40))
     w = wl.paper_1mp(W=512, H=512)
     A, B = w.render()
     sc = w.schedule
