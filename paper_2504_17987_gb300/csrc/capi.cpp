@@ -193,6 +193,9 @@ struct rpiv_handle {
     cudaEvent_t done_ev = nullptr;
     bool done_recorded = false;
     cudaStream_t cap_stream = nullptr;
+    // a second capture stream and the fork / join events of a split batch
+    cudaStream_t cap_stream2 = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::map<std::string, cudaGraphExec_t> graphs;
     char *adj_ws = nullptr;
     size_t adj_bytes = 0;
@@ -281,14 +284,17 @@ std::string stage_tag(const rpiv_handle *h, const StageDef &d)
 }
 
 // The full schedule for n pairs whose pointers are in h->io_dev.
-rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred, bool any_nopred, cudaStream_t st)
+// The launch sequence of pairs pair0 .. pair0 + n - 1 of the call.
+rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred, bool any_nopred, cudaStream_t st,
+                             int pair0 = 0)
 {
     const rpiv_config &c = h->cfg;
     const int L = c.predictor_levels;
     const long long ps = (long long)h->pair_stride;
-    const PairIO *io = h->io_dev;
+    const PairIO *io = h->io_dev + pair0;
     const long long ios = sizeof(PairIO);
-    auto ws = [&](size_t off) { return ptr_direct(h->ws + off, ps); };
+    char *const wbase = h->ws + (size_t)pair0 * h->pair_stride;
+    auto ws = [&](size_t off) { return ptr_direct(wbase + off, ps); };
     auto tab = [&](const void *field) { return ptr_table(field, ios); };
     const int user_fmt = c.fmt == RPIV_U8 ? PIX_U8 : (c.fmt == RPIV_U16 ? PIX_U16 : PIX_F32);
     const StageDef &p0 = h->stages[L];
@@ -737,8 +743,12 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
             return cleanup(RPIV_ERR_CUDA, "event creation failed");
     if ((e = cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming)) != cudaSuccess)
         return cleanup(RPIV_ERR_CUDA, "event creation failed");
-    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking)) != cudaSuccess)
         return cleanup(RPIV_ERR_CUDA, "stream creation failed");
+    if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cleanup(RPIV_ERR_CUDA, "event creation failed");
     *out = h;
     g_err.clear();
     return RPIV_OK;
@@ -757,6 +767,15 @@ rpiv_status rpiv_workspace_bytes(const rpiv_handle *h, size_t *bytes)
     if (!h || !bytes) return fail(RPIV_ERR_INVALID_ARG, "null argument");
     *bytes = h->ws_bytes + sizeof(PairIO) * h->cfg.max_batch + h->adj_bytes;
     return RPIV_OK;
+}
+
+// Captured batches of 16 pairs and more run as two halves on forked streams
+// (RPIV_SPLIT_BATCH=0 keeps one chain; read when a batch shape is captured).
+static bool split_batch(int n)
+{
+    if (n < 16) return false;
+    const char *e = std::getenv("RPIV_SPLIT_BATCH");
+    return !(e && std::strcmp(e, "0") == 0);
 }
 
 rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, const void *const *img_b,
@@ -821,7 +840,25 @@ rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, 
         cudaGraph_t graph = nullptr;
         CK(cudaStreamSynchronize(st), "first-run synchronise");
         CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        rs = enqueue_schedule(h, n, pitch_bytes, any_pred, any_nopred, h->cap_stream);
+        if (split_batch(n)) {
+            // two independent halves on forked streams of one graph: one half's
+            // small launches and wave tails overlap the other's large passes
+            const int n0 = (n + 1) / 2;
+            cudaError_t fe = cudaEventRecord(h->fork_ev, h->cap_stream);
+            if (fe == cudaSuccess) fe = cudaStreamWaitEvent(h->cap_stream2, h->fork_ev, 0);
+            rs = fe == cudaSuccess ? enqueue_schedule(h, n0, pitch_bytes, any_pred, any_nopred, h->cap_stream, 0)
+                                   : cuda_fail(fe, "capture fork");
+            if (rs == RPIV_OK)
+                rs = enqueue_schedule(h, n - n0, pitch_bytes, any_pred, any_nopred, h->cap_stream2, n0);
+            if (fe == cudaSuccess) {
+                // the join also ends the second stream's part in the capture on every path
+                cudaError_t je = cudaEventRecord(h->join_ev, h->cap_stream2);
+                if (je == cudaSuccess) je = cudaStreamWaitEvent(h->cap_stream, h->join_ev, 0);
+                if (je != cudaSuccess && rs == RPIV_OK) rs = cuda_fail(je, "capture join");
+            }
+        } else {
+            rs = enqueue_schedule(h, n, pitch_bytes, any_pred, any_nopred, h->cap_stream);
+        }
         cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
         if (rs != RPIV_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -993,6 +1030,9 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
             if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
         if (h->done_ev) cudaEventDestroy(h->done_ev);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+        if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+        if (h->join_ev) cudaEventDestroy(h->join_ev);
         if (h->ws) cudaFree(h->ws);
         if (h->err_dev) cudaFree(h->err_dev);
         if (h->io_dev) cudaFree(h->io_dev);

@@ -281,6 +281,27 @@ def test_pipeline_supplied_predictor_and_batch_equals_single(form, monkeypatch):
     eng.close()
 
 
+def test_split_batch_equals_pairs_alone():
+    # batches of 16 pairs and more are captured as two halves on forked streams
+    wk = wl.paper_1mp(W=512, H=512)
+    sc = wk.schedule
+    cfg = rp.Config.from_schedule(512, 512, sc, bit_depth=12, max_batch=16)
+    eng = rp.Engine(cfg)
+    pairs = []
+    for k in range(16):
+        A, B = wl.paper_1mp(W=512, H=512, seed=2000 + k).render()
+        pairs.append((dev(A), dev(B)))
+    alone = [[t.clone() for t in eng.process_pair(a, b)] for a, b in pairs]
+    outs = eng.process_batch([p[0] for p in pairs], [p[1] for p in pairs])  # eager first run
+    again = eng.process_batch([p[0] for p in pairs], [p[1] for p in pairs])  # the split graph
+    torch.cuda.synchronize()
+    for i in range(16):
+        for k in range(4):
+            assert torch.equal(outs[k][i], alone[i][k]), (i, k)
+            assert torch.equal(again[k][i], alone[i][k]), (i, k)
+    eng.close()
+
+
 def test_pipeline_bf16_within_0p01_px():
     w = wl.paper_1mp(W=512, H=512)
     A, B = w.render()
