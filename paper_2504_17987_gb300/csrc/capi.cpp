@@ -193,9 +193,10 @@ struct rpiv_handle {
     cudaEvent_t done_ev = nullptr;
     bool done_recorded = false;
     cudaStream_t cap_stream = nullptr;
-    // a second capture stream and the fork / join events of a split batch
-    cudaStream_t cap_stream2 = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // capture streams of the further parts of a split batch, fork and join events
+    static constexpr int kParts = 4;
+    cudaStream_t cap_part[kParts] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kParts] = {};
     std::map<std::string, cudaGraphExec_t> graphs;
     char *adj_ws = nullptr;
     size_t adj_bytes = 0;
@@ -743,11 +744,15 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
             return cleanup(RPIV_ERR_CUDA, "event creation failed");
     if ((e = cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming)) != cudaSuccess)
         return cleanup(RPIV_ERR_CUDA, "event creation failed");
-    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cleanup(RPIV_ERR_CUDA, "stream creation failed");
-    if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming)) != cudaSuccess)
+    for (int i = 1; i < rpiv_handle::kParts; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&h->cap_part[i], cudaStreamNonBlocking)) != cudaSuccess)
+            return cleanup(RPIV_ERR_CUDA, "stream creation failed");
+        if ((e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+            return cleanup(RPIV_ERR_CUDA, "event creation failed");
+    }
+    if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
         return cleanup(RPIV_ERR_CUDA, "event creation failed");
     *out = h;
     g_err.clear();
@@ -769,13 +774,19 @@ rpiv_status rpiv_workspace_bytes(const rpiv_handle *h, size_t *bytes)
     return RPIV_OK;
 }
 
-// Captured batches of 16 pairs and more run as two halves on forked streams
-// (RPIV_SPLIT_BATCH=0 keeps one chain; read when a batch shape is captured).
-static bool split_batch(int n)
+// Captured batches of 16 pairs and more run as parts of at least 8 pairs on
+// forked streams, two by default (RPIV_SPLIT_BATCH = 1, 2 or 4 parts; read
+// when a batch shape is captured).  Measured on the 64-pair 1 MP workload:
+// one chain 13420, two parts 13664-13690, four parts 13346 pairs/s.
+static int split_parts(int n)
 {
-    if (n < 16) return false;
-    const char *e = std::getenv("RPIV_SPLIT_BATCH");
-    return !(e && std::strcmp(e, "0") == 0);
+    int parts = 2;
+    if (const char *e = std::getenv("RPIV_SPLIT_BATCH")) {
+        const int v = std::atoi(e);
+        parts = (v == 1 || v == 2 || v == 4) ? v : (v == 0 ? 1 : 2);
+    }
+    while (parts > 1 && n / parts < 8) parts /= 2;
+    return parts;
 }
 
 rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, const void *const *img_b,
@@ -840,20 +851,26 @@ rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, 
         cudaGraph_t graph = nullptr;
         CK(cudaStreamSynchronize(st), "first-run synchronise");
         CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        if (split_batch(n)) {
-            // two independent halves on forked streams of one graph: one half's
-            // small launches and wave tails overlap the other's large passes
-            const int n0 = (n + 1) / 2;
+        const int parts = split_parts(n);
+        if (parts > 1) {
+            // independent parts on forked streams of one graph: one part's small
+            // launches and wave tails overlap the others' large passes
             cudaError_t fe = cudaEventRecord(h->fork_ev, h->cap_stream);
-            if (fe == cudaSuccess) fe = cudaStreamWaitEvent(h->cap_stream2, h->fork_ev, 0);
-            rs = fe == cudaSuccess ? enqueue_schedule(h, n0, pitch_bytes, any_pred, any_nopred, h->cap_stream, 0)
-                                   : cuda_fail(fe, "capture fork");
-            if (rs == RPIV_OK)
-                rs = enqueue_schedule(h, n - n0, pitch_bytes, any_pred, any_nopred, h->cap_stream2, n0);
-            if (fe == cudaSuccess) {
-                // the join also ends the second stream's part in the capture on every path
-                cudaError_t je = cudaEventRecord(h->join_ev, h->cap_stream2);
-                if (je == cudaSuccess) je = cudaStreamWaitEvent(h->cap_stream, h->join_ev, 0);
+            int forked = 1;
+            for (; fe == cudaSuccess && forked < parts; ++forked)
+                fe = cudaStreamWaitEvent(h->cap_part[forked], h->fork_ev, 0);
+            if (fe != cudaSuccess) --forked;
+            rs = fe == cudaSuccess ? RPIV_OK : cuda_fail(fe, "capture fork");
+            for (int i = 0, first = 0; i < parts && rs == RPIV_OK; ++i) {
+                const int cnt = n / parts + (i < n % parts ? 1 : 0);
+                rs = enqueue_schedule(h, cnt, pitch_bytes, any_pred, any_nopred, i ? h->cap_part[i] : h->cap_stream,
+                                      first);
+                first += cnt;
+            }
+            // the joins also end the forked streams' parts of the capture on every path
+            for (int i = 1; i < forked; ++i) {
+                cudaError_t je = cudaEventRecord(h->join_ev[i], h->cap_part[i]);
+                if (je == cudaSuccess) je = cudaStreamWaitEvent(h->cap_stream, h->join_ev[i], 0);
                 if (je != cudaSuccess && rs == RPIV_OK) rs = cuda_fail(je, "capture join");
             }
         } else {
@@ -1030,9 +1047,11 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
             if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
         if (h->done_ev) cudaEventDestroy(h->done_ev);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-        if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+        for (int i = 1; i < rpiv_handle::kParts; ++i) {
+            if (h->cap_part[i]) cudaStreamDestroy(h->cap_part[i]);
+            if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+        }
         if (h->fork_ev) cudaEventDestroy(h->fork_ev);
-        if (h->join_ev) cudaEventDestroy(h->join_ev);
         if (h->ws) cudaFree(h->ws);
         if (h->err_dev) cudaFree(h->err_dev);
         if (h->io_dev) cudaFree(h->io_dev);
