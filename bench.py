@@ -818,11 +818,19 @@ def main():
 
 
 def _kernel_source_hash() -> str:
+    """Hash of the pass kernels' code with comments and whitespace removed, so
+    that stored DRAM counters stay tied to the code they were taken on and
+    survive edits to comments alone."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("pass_impl.cuh", "k_pass_fp32.cu", "k_pass_bf16.cu", "k_pass_fp16.cu", "pass_plan.cpp"):
-        with open(os.path.join(ROOT, "paper_2504_17987_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2504_17987_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
+        h.update(text.encode())
     return h.hexdigest()[:16]
 
 

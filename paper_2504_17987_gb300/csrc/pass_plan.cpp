@@ -231,9 +231,9 @@ int min_ctas(int w, int R, int prec)
 bool plan_search(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *plan)
 {
     // registers per thread as the kernels are built: the FP32 kernel is bounded
-    // to five CTAs per SM up to r = 4 (48 registers), three beyond and for the
-    // kernel specialised to 64 px windows at 50 % overlap; the tensor-core
-    // kernel to three
+    // to five CTAs per SM up to r = 4 (48 registers), three beyond, for the
+    // kernel specialised to 64 px windows at 50 % overlap and for 16 px windows
+    // at r = 4; the tensor-core kernel to three
     const bool wide = (w == 64 && s == 32 && (R == 1 || R == 4)) || (w == 16 && s == 8 && R == 4);
     const int regs = (prec == PREC_FP32 && R <= 4 && !wide) ? 48 : 80;
     const int by_regs = 65536 / (regs * kThreads), by_threads = 2048 / kThreads;
