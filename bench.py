@@ -469,31 +469,49 @@ def run_adjoint(args):
 # --------------------------------------------------------------- clocks --
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi samples every 20 ms around the timed region.  Sampling is
+    live before the region starts (the first sample has arrived), and the
+    summary keeps the samples whose timestamps fall between mark_start() and
+    mark_end(); a region shorter than one interval falls back to the samples
+    nearest to it, and says so."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
         self.th = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            deadline = time.monotonic() + 10.0
+            while not self.lines and self.proc.poll() is None and time.monotonic() < deadline:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        # one more interval, so that a sample taken at the very end is read
+        time.sleep(2 * self.INTERVAL_MS / 1000.0)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -505,25 +523,46 @@ class ClockSampler:
         if self.th is not None:
             self.th.join(timeout=2)
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+    @staticmethod
+    def _stamp(text, arrived):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return arrived
+
+    def _parse(self):
+        rows = []
+        for arrived, ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                sm, mx = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[4:8]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+            reasons = {nm for nm, val in zip(self.REASONS, parts[5:9]) if val.lower().startswith("active")}
+            rows.append((self._stamp(parts[0], arrived), sm, mx, reasons))
+        return rows
+
+    def summary(self):
+        rows = self._parse()
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "interval_ms": self.INTERVAL_MS}
+        out = {"interval_ms": self.INTERVAL_MS}
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+            out["window_ms"] = round((self.t1 - self.t0) * 1000.0, 1)
+            if not inside:
+                before = [r for r in rows if r[0] < self.t0][-1:]
+                after = [r for r in rows if r[0] > self.t1][:1]
+                inside = before + after
+                out["nearest_outside_region"] = True
+            rows = inside
+        out.update({"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                    "reasons": sorted(set().union(*(r[3] for r in rows))), "samples": len(rows)})
+        return out
 
 
 # ---------------------------------------------------------------- ours --
@@ -631,7 +670,9 @@ def main():
         for _ in range(args.warmup):
             step()
         with ClockSampler(local) as cs:
+            cs.mark_start()
             ms = timed_replicas(step, args.steps, 0, barrier, start_timer, max_over_ranks)
+            cs.mark_end()
         if prec == args.headline:
             clocks = cs.summary()
         fields[prec] = (outs[0][0].cpu().numpy(), outs[1][0].cpu().numpy())

@@ -1,5 +1,6 @@
 """Host logic of bench.py that needs no device: the source hash that ties the
-stored DRAM counters to the pass kernels' code."""
+stored DRAM counters to the pass kernels' code, and the summary of the clock
+samples taken around the timed region."""
 import os
 import shutil
 
@@ -38,3 +39,39 @@ def test_source_hash_ignores_comments_and_whitespace_but_not_code(tmp_path, monk
     impl = dst / "pass_impl.cuh"
     impl.write_text(impl.read_text() + "\nstatic int added_code = 1;\n")
     assert bench._kernel_source_hash() != h0
+
+
+def _smi_line(t, sm, reason="Not Active"):
+    import datetime
+    stamp = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return f"{stamp}, {sm}, 2070, 900.00, 0x0000000000000000, {reason}, Not Active, Not Active, Not Active"
+
+
+def test_clock_summary_keeps_the_samples_inside_the_timed_region():
+    cs = bench.ClockSampler(0)
+    base = 1_700_000_000.0
+    cs.lines = [(base + 0.02 * k, _smi_line(base + 0.02 * k, 1200 if k < 5 or k > 12 else 2070,
+                                            "Active" if k == 2 else "Not Active")) for k in range(16)]
+    cs.t0, cs.t1 = base + 0.095, base + 0.245
+    out = cs.summary()
+    assert out["samples"] == 8 and out["sm_mhz"] == 2070 and out["reasons"] == []
+    assert "nearest_outside_region" not in out and out["window_ms"] == 150.0
+    # a slowdown inside the region is reported
+    cs.t0 = base + 0.035
+    assert cs.summary()["reasons"] == ["hw_slowdown"]
+
+
+def test_clock_summary_of_a_region_shorter_than_the_interval_uses_the_nearest_samples():
+    cs = bench.ClockSampler(0)
+    base = 1_700_000_000.0
+    cs.lines = [(base, _smi_line(base, 2070)), (base + 0.5, _smi_line(base + 0.5, 2050)),
+                (base + 1.0, _smi_line(base + 1.0, 1000))]
+    cs.t0, cs.t1 = base + 0.6, base + 0.7
+    out = cs.summary()
+    assert out["nearest_outside_region"] and out["samples"] == 2 and out["sm_mhz"] == 1525.0
+    # no region marked: every sample counts
+    cs.t0 = cs.t1 = None
+    assert cs.summary()["samples"] == 3
+    # unparseable output gives no clock rather than a wrong one
+    cs.lines = [(base, "[N/A], [N/A]")]
+    assert cs.summary()["sm_mhz"] is None
