@@ -327,17 +327,20 @@ __device__ __forceinline__ float inv_norm(float s1, float s2, float inv_n, float
 //   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]         (threads along r, odd pitch)
 // so V[r][c] is the sum over the w x w box whose top-left logical B' pixel
 // is (r, c); the second plane keeps 1 / sqrt(E_B) of the box instead of its
-// sum of squares.  Each thread restarts its running sum every 8 outputs.
+// sum of squares.  Each thread keeps a running sum over box_lv (columns) or
+// box_lh (rows) outputs; the plan sets them and the number of runs for a full
+// tile, and an edge tile, never larger, skips the runs that start past its end.
 static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
 {
     const PassPlan &P = a.plan;
     const int w = g.w, tid = threadIdx.x;
     const int cp = P.h_pitch;  // pitch of C and V (odd)
     float *C1 = Cs, *C2 = Cs + g.vh * cp;
-    const int nsegv = (g.vh + 7) / 8;
-    for (int it = tid; it < g.BC * nsegv; it += blockDim.x) {
+    const int Lv = P.box_lv;
+    for (int it = tid; it < g.BC * P.box_nv; it += blockDim.x) {
         const int seg = it / g.BC, x = it - seg * g.BC;
-        const int r_lo = seg * 8, r_hi = min(g.vh, r_lo + 8);
+        const int r_lo = seg * Lv, r_hi = min(g.vh, r_lo + Lv);
+        if (r_lo >= g.vh) continue;
         const float *col = Bs + g.OFFB + x;
         float s1 = 0.f, s2 = 0.f;
         for (int y = r_lo; y < r_lo + w; ++y) {
@@ -359,10 +362,11 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
     const int vp = P.v_pitch;  // pitch of V (odd, >= hw)
     const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
     float *V1 = Vs, *VN = Vs + g.vh * vp;
-    const int nsegh = (g.hw + 7) / 8;
-    for (int it = tid; it < g.vh * nsegh; it += blockDim.x) {
+    const int Lh = P.box_lh;
+    for (int it = tid; it < g.vh * P.box_nh; it += blockDim.x) {
         const int seg = it / g.vh, r = it - seg * g.vh;
-        const int c_lo = seg * 8, c_hi = min(g.hw, c_lo + 8);
+        const int c_lo = seg * Lh, c_hi = min(g.hw, c_lo + Lh);
+        if (c_lo >= g.hw) continue;
         const float *c1 = C1 + r * cp, *c2 = C2 + r * cp;
         float s1 = 0.f, s2 = 0.f;
         for (int x = c_lo; x < c_lo + w; ++x) {

@@ -79,6 +79,24 @@ struct Layout {
 
 // strip: a one-row tile whose CTA walks window rows; its block planes live in
 // a two-row ring outside the reused region, since they outlive a step
+// Outputs per running sum of a box-sum pass, for n outputs along a run and
+// `across` runs side by side: 8, unless a longer run (up to 16) brings all
+// runs into one round of the CTA's threads and still keeps 7/8 of them busy.
+// Each run starts with a full w-term sum, and a longer run of add/subtract
+// updates drifts further.  Measured per 64-pair 1 MP launch: 16 px tiles
+// (410 -> 246 column runs, 315 -> 245 row runs) 1.200 -> 1.158 ms; runs
+// that left threads idle were slower (strips of 32 px windows, 308 -> 154
+// column runs, 0.993 -> 1.033 ms).
+int box_run(int n, int across)
+{
+    const int runs = kThreads / across;
+    if (runs < 1) return 8;
+    const int L = (n + runs - 1) / runs;
+    if (L <= 8 || L > 16) return 8;
+    const int items = across * ((n + L - 1) / L);
+    return 8 * items >= 7 * kThreads ? L : 8;
+}
+
 Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool strip = false)
 {
     PassPlan p;
@@ -104,6 +122,10 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool str
     p.b_pitch = odd4(p.padl + aw + R + 4);
     p.h_pitch = BC | 1;
     p.v_pitch = (BC - w + 1) | 1;
+    p.box_lv = box_run(vh, BC);
+    p.box_lh = box_run(BC - w + 1, vh);
+    p.box_nv = (vh + p.box_lv - 1) / p.box_lv;
+    p.box_nh = (BC - w + 1 + p.box_lh - 1) / p.box_lh;
     if (prec == PREC_FP32) {
         // row groups per block: enough (block, sy, row-group) items to fill the
         // CTA; a power of two dividing G, so that a group's partial planes sit

@@ -70,6 +70,8 @@ struct PassPlan {
                      // the previous block row's planes (tiles_y counts the strip segments)
     int RGx;      // row groups per block in the plane phase
     int pstride;  // floats between consecutive blocks' planes
+    int box_lv, box_lh;  // outputs per running sum in the column and row box-sum passes
+    int box_nv, box_nh;  // running sums per column and per row of a full tile (edge tiles skip the ones past their end)
     // shared-memory layout (byte offsets) for a full tile
     int smem_bytes;
     int off_a, a_pitch;          // A region, floats
