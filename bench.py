@@ -799,16 +799,7 @@ def main():
         bound = "tensor"
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         peak_src = "measured (MEASURED_PEAKS.json bf16_tflops_sustained)" if peaks else "fallback"
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        key = f"{head}/{dom['name']}"
-        ent = tr.get(key)
-        src_hash = _kernel_source_hash()
-        if ent and ent.get("source_hash") == src_hash:
-            traffic = ent["bytes_per_pair"] * dom["pairs"]
-    except Exception:
-        traffic = None
+    traffic = stored_traffic(args.workload, head, dom)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"pass_kernel {dom['name']} (w={dom['window']}, s={dom['step']}, "
                 f"r={dom['radius']}, {dom['pairs']} pairs/launch)", "peak_source": peak_src,
@@ -856,6 +847,24 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def stored_traffic(workload: str, head: str, dom: dict, path: str | None = None):
+    """DRAM bytes per launch of the dominant pass from ncu counters stored in
+    profiles/traffic.json, or None.  An entry counts only for the workload,
+    precision and pass it was taken on, with the same window, step and radius,
+    and while the pass kernels' code is the code it was taken on."""
+    try:
+        with open(path or os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tr = json.load(fh)
+        ent = tr.get(f"{workload}/{head}/{dom['name']}")
+        if (ent and ent.get("source_hash") == _kernel_source_hash()
+                and (ent.get("window"), ent.get("step"), ent.get("radius")) ==
+                (dom["window"], dom["step"], dom["radius"])):
+            return ent["bytes_per_pair"] * dom["pairs"]
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return None
 
 
 def _kernel_source_hash() -> str:

@@ -75,3 +75,31 @@ def test_clock_summary_of_a_region_shorter_than_the_interval_uses_the_nearest_sa
     # unparseable output gives no clock rather than a wrong one
     cs.lines = [(base, "[N/A], [N/A]")]
     assert cs.summary()["sm_mhz"] is None
+
+
+def test_stored_traffic_applies_only_to_the_pass_it_was_taken_on(tmp_path):
+    import json
+    h = bench._kernel_source_hash()
+    entry = {"bytes_per_pair": 1000.0, "source_hash": h, "window": 64, "step": 32, "radius": 4}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps({"paper_1mp/fp32/pass/p0": entry}))
+    dom = {"name": "pass/p0", "window": 64, "step": 32, "radius": 4, "pairs": 64}
+    assert bench.stored_traffic("paper_1mp", "fp32", dom, str(path)) == 64000.0
+    # another workload's pass of the same name (a 32 px pass there) gets nothing
+    assert bench.stored_traffic("paper_1mp_r1", "fp32", dict(dom, window=32, step=16), str(path)) is None
+    assert bench.stored_traffic("paper_1mp_r1", "fp32", dom, str(path)) is None
+    # nor another precision, another geometry, or changed kernels
+    assert bench.stored_traffic("paper_1mp", "bf16", dom, str(path)) is None
+    assert bench.stored_traffic("paper_1mp", "fp32", dict(dom, radius=1), str(path)) is None
+    path.write_text(json.dumps({"paper_1mp/fp32/pass/p0": dict(entry, source_hash="0" * 16)}))
+    assert bench.stored_traffic("paper_1mp", "fp32", dom, str(path)) is None
+    assert bench.stored_traffic("paper_1mp", "fp32", dom, str(tmp_path / "missing.json")) is None
+
+
+def test_committed_traffic_entries_name_their_geometry():
+    import json
+    tr = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for key, ent in tr.items():
+        workload, head, _, name = key.split("/")
+        assert workload in ("paper_1mp", "paper_1mp_r1") and head in ("fp32", "bf16", "fp16")
+        assert {"window", "step", "radius", "bytes_per_pair", "source_hash"} <= set(ent)
