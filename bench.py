@@ -14,6 +14,7 @@ Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import multiprocessing as mp
 import os
@@ -525,7 +526,6 @@ class ClockSampler:
 
     @staticmethod
     def _stamp(text, arrived):
-        import datetime
         try:
             return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
         except ValueError:
