@@ -384,15 +384,18 @@ def process_pair(A, B, windows: Sequence[int], overlaps: Sequence[float], radii:
     return PipelineResult(uu, vv, om, mk, trace)
 
 
-def refine(A, B, w: int, s: int, u0, v0, steps: int = 5, eta0: float = 0.25, halvings: int = 3):
-    """Gradient-ascent refinement of the score (differentiation pattern).
+def ascend(f, u0, v0, steps: int = 5, eta0: float = 0.25, halvings: int = 3):
+    """The refinement's step rule on any score: f(u, v) -> (S, gu, gv), and
+    f(u, v, grad=False) -> S.
 
-    Rule: g0 = grad S at the start; step k uses eta_k = eta0 * 0.5^k / max|g0|
-    along the current gradient; a step is accepted only if S increases, else
-    eta is halved, at most `halvings` times.  Returns (u, v, [S after each step]).
+    g0 = grad S at the start; step k moves along the current gradient with
+    eta_k = eta0 * 0.5^k / max|g0|; the step is accepted only if S increases,
+    otherwise eta is halved and the step retried, at most `halvings` times
+    (the field stays where it was if every try fails).  Returns
+    (u, v, [S at the start and after each step]).
     """
     u = _f64(u0).copy(); v = _f64(v0).copy()
-    S, gu, gv = score_grad(A, B, w, s, u, v)
+    S, gu, gv = f(u, v)
     gmax = max(float(np.max(np.abs(gu))), float(np.max(np.abs(gv))))
     hist = [S]
     if gmax == 0.0:
@@ -401,11 +404,19 @@ def refine(A, B, w: int, s: int, u0, v0, steps: int = 5, eta0: float = 0.25, hal
         eta = eta0 * 0.5 ** k / gmax
         for _ in range(halvings + 1):
             cu, cv = u + eta * gu, v + eta * gv
-            Sc = score_grad(A, B, w, s, cu, cv, grad=False)
+            Sc = f(cu, cv, grad=False)
             if Sc > S:
                 u, v, S = cu, cv, Sc
                 break
             eta *= 0.5
-        S, gu, gv = score_grad(A, B, w, s, u, v)
+        S, gu, gv = f(u, v)
         hist.append(S)
     return u, v, hist
+
+
+def refine(A, B, w: int, s: int, u0, v0, steps: int = 5, eta0: float = 0.25, halvings: int = 3):
+    """Gradient-ascent refinement of the correlation score S (differentiation
+    pattern): ascend() on score_grad of the pair."""
+    def f(u, v, grad=True):
+        return score_grad(A, B, w, s, u, v, grad=grad)
+    return ascend(f, u0, v0, steps, eta0, halvings)

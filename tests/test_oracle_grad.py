@@ -115,3 +115,48 @@ def test_refinement_rule_increases_the_score():
     assert len(hist) == 6
     assert all(b >= a for a, b in zip(hist, hist[1:]))
     assert hist[-1] > hist[0]
+
+
+def _quadratic(a, b):
+    """S(u, v) = -(u - a)^2 - (v - b)^2 on a one-node field, with its gradient."""
+    def f(u, v, grad=True):
+        S = float(-np.sum((u - a) ** 2) - np.sum((v - b) ** 2))
+        if not grad:
+            return S
+        return S, -2.0 * (u - a), -2.0 * (v - b)
+    return f
+
+
+def test_refinement_step_rule_follows_a_hand_computed_trace():
+    # S = -(u - 1)^2 - (v - 0.5)^2 from (0, 0), eta0 = 3: g0 = (2, 1), max|g0| = 2.
+    # k = 0: eta = 1.5 -> (3, 1.5), S = -5 < -1.25: halved; eta = 0.75 -> (1.5, 0.75), S = -0.3125, taken.
+    # k = 1: g = (-1, -0.5), eta = 0.75 -> (0.75, 0.375), S = -0.078125, taken.
+    # k = 2: g = (0.5, 0.25), eta = 0.375 -> (0.9375, 0.46875), S = -0.0048828125, taken.
+    u, v, hist = oracle.ascend(_quadratic(1.0, 0.5), np.zeros((1, 1)), np.zeros((1, 1)), steps=3, eta0=3.0)
+    assert hist == [-1.25, -0.3125, -0.078125, -0.0048828125]
+    assert u[0, 0] == 0.9375 and v[0, 0] == 0.46875
+    # a rule without the 0.5^k decay, or scaled by max|g_k| instead of max|g0|,
+    # takes (1.5, 0.75) at k = 2 and ends at (1.125, 0.5625)
+
+
+def test_refinement_keeps_the_field_when_every_halving_fails():
+    # at the maximum the gradient is zero after the first step: S cannot increase,
+    # all 1 + 3 tries fail and the field stays, the history repeats
+    u, v, hist = oracle.ascend(_quadratic(1.0, 0.5), np.zeros((1, 1)), np.zeros((1, 1)), steps=3, eta0=2.0)
+    # k = 0: eta = 1 -> (2, 1), S = -1.25 is not above -1.25: halved; eta = 0.5 -> (1, 0.5), S = 0, taken
+    assert hist == [-1.25, 0.0, 0.0, 0.0]
+    assert u[0, 0] == 1.0 and v[0, 0] == 0.5
+
+
+def test_refinement_halves_at_most_three_times():
+    # S = -(u - 1)^2, g0 = 2 at u = 0, eta0 = 40: the tries move u to 2 eta and
+    # are taken only for 0 < eta < 1; eta runs 20, 10, 5, 2.5 (three halvings),
+    # then 1.25 (a fourth) and 0.625 (a fifth, taken: u = 1.25, S = -0.0625)
+    f = _quadratic(1.0, 0.0)
+    z = np.zeros((1, 1))
+    u, _, hist = oracle.ascend(f, z, z, steps=1, eta0=40.0)
+    assert hist == [-1.0, -1.0] and u[0, 0] == 0.0
+    u, _, hist = oracle.ascend(f, z, z, steps=1, eta0=40.0, halvings=4)
+    assert hist == [-1.0, -1.0] and u[0, 0] == 0.0
+    u, _, hist = oracle.ascend(f, z, z, steps=1, eta0=40.0, halvings=5)
+    assert hist == [-1.0, -0.0625] and u[0, 0] == 1.25
