@@ -469,6 +469,37 @@ def run_adjoint(args):
 
 # --------------------------------------------------------------- clocks --
 
+def measure_fma_peak(index: int, reps: int = 30) -> dict:
+    """The FP32 CUDA-core peak measured by the FMA-throughput microbenchmark
+    (libfmapeak: 16 independent FMA chains per thread, 8 CTAs of 256 threads on
+    every SM), the shortest of `reps` launches, with the SM clock sampled while
+    it runs; also the rate per SM and clock, to compare with the 128 FP32 lanes
+    x 2 flop of the architecture."""
+    import ctypes
+
+    import torch
+
+    from paper_2504_17987_gb300 import build as b
+    lib = ctypes.CDLL(b.build_fma_peak())
+    lib.fma_peak_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    best, flops = ctypes.c_float(), ctypes.c_double()
+    st = torch.cuda.current_stream()
+    with ClockSampler(index) as cs:
+        cs.mark_start()
+        rc = lib.fma_peak_run(8, 8192, reps, ctypes.byref(best), ctypes.byref(flops), ctypes.c_void_p(st.cuda_stream))
+        cs.mark_end()
+    if rc != 0:
+        raise RuntimeError(f"FMA microbenchmark failed: CUDA error {rc}")
+    clk = cs.summary()
+    sms = torch.cuda.get_device_properties(index).multi_processor_count
+    tflops = flops.value / (best.value / 1e3) / 1e12
+    mhz = (clk or {}).get("sm_mhz") or None
+    per_clk = (tflops * 1e12 / (sms * mhz * 1e6)) if mhz else None
+    return {"tflops": tflops, "best_ms": best.value, "flops_per_launch": flops.value, "sms": sms,
+            "flop_per_sm_per_clock": per_clk, "clocks": clk}
+
+
 class ClockSampler:
     """nvidia-smi samples every 20 ms around the timed region.  Sampling is
     live before the region starts (the first sample has arrived), and the
@@ -792,9 +823,14 @@ def main():
     except Exception:
         pass
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_derived = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    fma = measure_fma_peak(local)
     if head == "fp32":
-        bound, peak, peak_src = "alu", fp32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        bound, peak = "alu", fma["tflops"]
+        peak_src = (f"measured: FMA microbenchmark {fma['tflops']:.1f} TFLOP/s at "
+                    f"{(fma['clocks'] or {}).get('sm_mhz')} MHz (derived {sms} SMs x 128 lanes x 2 x "
+                    f"{sm_max:.0f} MHz = {fp32_derived:.1f})")
     else:
         bound = "tensor"
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -805,7 +841,8 @@ def main():
                 f"r={dom['radius']}, {dom['pairs']} pairs/launch)", "peak_source": peak_src,
                 "per_launch_ms": per_launch_ms, "algorithmic_flops_per_launch": direct_flops,
                 "executed_flops_per_launch": plane_flops,
-                "executed_frac": plane_flops / (per_launch_ms / 1000.0) / 1e12 / peak}
+                "executed_frac": plane_flops / (per_launch_ms / 1000.0) / 1e12 / peak,
+                "fp32_fma_peak": fma, "fp32_derived_peak_tflops": fp32_derived}
     stage_ms = {r["name"]: r["total_ms"] / r["launches"] for r in recs}
     launches_per_step = sum(r["launches"] for r in recs) / 3.0
 
@@ -874,7 +911,7 @@ def _kernel_source_hash() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("pass_impl.cuh", "k_pass_fp32.cu", "k_pass_bf16.cu", "k_pass_fp16.cu", "pass_plan.cpp"):
+    for f in ("pass_impl.cuh", "tc_pass.cuh", "k_pass_fp32.cu", "k_pass_tc.cu", "pass_plan.cpp"):
         with open(os.path.join(ROOT, "paper_2504_17987_gb300", "csrc", f), encoding="utf-8") as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)

@@ -157,6 +157,24 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
                           const float *u, const float *v, float grad_score, float *grad_u, float *grad_v,
                           float *score_out, void *cuda_stream);
 
+/* Gradient-ascent refinement of the field by the score of rpiv_backward (the
+ * differentiation pattern applied to the paper's correction, Sec. 2: the
+ * correlation coefficient of the warped pair is raised directly).  The step
+ * rule: g0 = dS/d(u, v) at the start; step k moves along the current
+ * gradient by eta_k = eta0 * 0.5^k / max|g0|; a step is kept only if S
+ * increases, otherwise eta is halved and the step retried, at most
+ * `halvings` times (the field stays where it was if every try fails).
+ *   u, v     device float arrays on pass 1's grid (window[0], overlap[0]),
+ *            read as the start and overwritten with the result.
+ *   hist     HOST float array of steps + 1 scores (the start, then after each
+ *            step), or NULL.
+ * Every score is read back to decide the step, so the call synchronises
+ * cuda_stream once per evaluation; it returns when the result is in u, v.
+ * Work buffers are owned by the handle (allocated on first use).
+ * Errors: INVALID_ARG (nulls, steps < 0, halvings < 0, eta0 <= 0), OOM, CUDA. */
+rpiv_status rpiv_refine(rpiv_handle *h, const void *img_a, const void *img_b, size_t pitch_bytes, float *u, float *v,
+                        int steps, float eta0, int halvings, float *hist, void *cuda_stream);
+
 /* Blocks until the handle's enqueued work has finished, polling for at most
  * timeout_ms milliseconds (host watchdog).  RPIV_ERR_TIMEOUT if it has not.  */
 rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms);
@@ -221,6 +239,19 @@ rpiv_status rpiv_stage_correlate(const void *img_a, const void *img_b, size_t pi
 rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius, rpiv_deform deform_mode,
                                                size_t *bytes);
 
+/* Status of the stage calls (rpiv_stage_correlate and its allocation-free
+ * form) queued on cuda_stream: waits for the stream with a host watchdog (at
+ * most timeout_ms), then reads and clears the device's stage error word.  Its
+ * kernels never wait without a limit: a copy or MMA completion that does not
+ * arrive in time makes the tile report its windows invalid (info 0, the
+ * predictor passed through) and sets the word.  The word is one per device,
+ * shared by every stage call on it, so a status covers all of them since the
+ * last read.  The correction step is the paper's (Sec. 2); the bounded waits
+ * and this status are this library's.
+ * Errors: TIMEOUT (the stream did not finish in time, or a bounded wait gave
+ * up), CUDA.                                                                 */
+rpiv_status rpiv_stage_status(void *cuda_stream, int timeout_ms);
+
 /* The same pass as rpiv_stage_correlate for callers that cannot allocate
  * device memory when they run it (no cudaMalloc/cudaFree or allocating
  * library call happens inside).  This entry point has no counterpart in the
@@ -230,8 +261,10 @@ rpiv_status rpiv_stage_correlate_scratch_bytes(int width, int height, int radius
  * the library, held by every GPU that loads the library until the process
  * exits; images needing more (rpiv_stage_correlate_scratch_bytes > 32 MiB,
  * about 2000 x 2000 pixels) are rejected with
- * RPIV_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All calls
+ * RPIV_ERR_INVALID_ARG.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing once the library's module is
+ * loaded on the device); the first call on a device loads it, so make that
+ * first call before any stream capture.  All calls
  * share the one array, so calls whose work overlaps on the GPU (different
  * streams, or other devices' calls are fine) race and must be serialised by
  * the caller; a later call on the same stream is ordered after the earlier.

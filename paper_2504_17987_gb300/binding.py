@@ -36,9 +36,9 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "
 PRECISIONS = {"fp32": RPIV_FP32, "bf16": RPIV_BF16, "fp16": RPIV_FP16}
 
 EXPORTED = sorted(["rpiv_config_default", "rpiv_validate_config", "rpiv_create", "rpiv_grid_shape",
-                   "rpiv_workspace_bytes", "rpiv_process_pair", "rpiv_process_batch", "rpiv_backward", "rpiv_wait",
-                   "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes",
-                   "rpiv_stage_correlate_noalloc", "rpiv_stage_validate",
+                   "rpiv_workspace_bytes", "rpiv_process_pair", "rpiv_process_batch", "rpiv_backward", "rpiv_refine",
+                   "rpiv_wait", "rpiv_destroy", "rpiv_last_error", "rpiv_stage_correlate", "rpiv_stage_correlate_scratch_bytes",
+                   "rpiv_stage_correlate_noalloc", "rpiv_stage_status", "rpiv_stage_validate",
                    "rpiv_stage_interp", "rpiv_stage_vorticity", "rpiv_stage_downsample", "rpiv_stage_ema",
                    "rpiv_stage_preprocess", "rpiv_stage_preprocess_scratch_bytes",
                    "rpiv_trace_enable", "rpiv_trace_read"])
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
     pa = ctypes.POINTER(vp)
     L.rpiv_process_batch.argtypes = [vp, i32, pa, pa, sz, pa, pa, pa, pa, pa, pa, vp]
     L.rpiv_backward.argtypes = [vp, vp, vp, sz, vp, vp, f32, vp, vp, vp, vp]
+    L.rpiv_refine.argtypes = [vp, vp, vp, sz, vp, vp, i32, f32, i32, ctypes.POINTER(f32), vp]
     L.rpiv_wait.argtypes = [vp, i32]
     L.rpiv_destroy.argtypes = [vp]
     L.rpiv_stage_correlate.argtypes = [vp, vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, sz,
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
     L.rpiv_stage_correlate_scratch_bytes.argtypes = [i32, i32, i32, i32, ctypes.POINTER(sz)]
     L.rpiv_stage_correlate_noalloc.argtypes = [vp, vp, sz, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp,
                                                vp, vp]
+    L.rpiv_stage_status.argtypes = [vp, i32]
     L.rpiv_stage_validate.argtypes = [vp, vp, vp, i32, i32, f32, f32, i32, vp, vp, vp, vp]
     L.rpiv_stage_interp.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp]
     L.rpiv_stage_vorticity.argtypes = [vp, vp, i32, i32, i32, vp, vp]
@@ -342,6 +344,13 @@ def _fmt_code(t: torch.Tensor) -> int:
     return RPIV_U8 if t.element_size() == 1 else RPIV_U16
 
 
+def stage_status(stream=None, timeout_ms: int = 10000):
+    """Raises RpivError (TIMEOUT) if a stage kernel's bounded wait gave up
+    since the last call, or the stream's work did not finish in time
+    (rpiv_stage_status)."""
+    _check(load().rpiv_stage_status(_stream(stream), int(timeout_ms)))
+
+
 def stage_correlate(a, b, w: int, s: int, r: int, pred_u=None, pred_v=None, precision: str = "fp32",
                     deform: str = "b", stream=None):
     """One correlation pass; returns (u, v, info) raw (pre-validation)."""
@@ -450,29 +459,16 @@ class CorrelationScore(torch.autograd.Function):
         return gu, gv, None, None, None
 
 
-def refine(engine: Engine, a, b, u0, v0, steps: int = 5, eta0: float = 0.25, halvings: int = 3):
-    """Gradient-ascent refinement of the correlation score: eta_k = eta0 0.5^k /
-    max|g0| along the current gradient, a step accepted only if S increases,
-    else eta halved up to `halvings` times.  Returns (u, v, [S per step])."""
-    u = u0.detach().clone().float()
-    v = v0.detach().clone().float()
-    S, gu, gv = engine.score_and_grad(a, b, u, v)
-    gmax = max(float(gu.abs().max()), float(gv.abs().max()))
-    hist = [float(S)]
-    if gmax == 0.0:
-        return u, v, hist
-    S = float(S)
-    for k in range(steps):
-        eta = eta0 * 0.5 ** k / gmax
-        for _ in range(halvings + 1):
-            cu, cv = u + eta * gu, v + eta * gv
-            Sc, _, _ = engine.score_and_grad(a, b, cu, cv, want_grad=False)
-            Sc = float(Sc)
-            if Sc > S:
-                u, v, S = cu, cv, Sc
-                break
-            eta *= 0.5
-        S_t, gu, gv = engine.score_and_grad(a, b, u, v)
-        S = float(S_t)
-        hist.append(S)
-    return u, v, hist
+def refine(engine: Engine, a, b, u0, v0, steps: int = 5, eta0: float = 0.25, halvings: int = 3, stream=None):
+    """Gradient-ascent refinement of the correlation score (rpiv_refine): eta_k
+    = eta0 0.5^k / max|g0| along the current gradient, a step kept only if S
+    increases, else eta halved up to `halvings` times.  Returns (u, v,
+    [S at the start and after each step])."""
+    _img_check(a, engine.cfg.fmt)
+    _img_check(b, engine.cfg.fmt)
+    u = u0.detach().clone().float().contiguous()
+    v = v0.detach().clone().float().contiguous()
+    hist = (ctypes.c_float * (steps + 1))()
+    _check(load().rpiv_refine(engine.handle, _ptr(a), _ptr(b), a.stride(0) * a.element_size(), _ptr(u), _ptr(v),
+                              int(steps), float(eta0), int(halvings), hist, _stream(stream)))
+    return u, v, [float(x) for x in hist]

@@ -15,9 +15,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(os.path.dirname(HERE), "_build", "rpiv")
 LIB = os.path.join(HERE, "librpiv.so")
 
-SOURCES = ["k_pass_fp32.cu", "k_pass_bf16.cu", "k_pass_fp16.cu", "k_deform.cu", "k_grid.cu", "k_adjoint.cu",
+SOURCES = ["k_pass_fp32.cu", "k_pass_tc.cu", "k_deform.cu", "k_grid.cu", "k_adjoint.cu",
            "k_static_scratch.cu", "k_pre.cu", "pass_plan.cpp", "capi.cpp"]
-HEADERS = ["rpiv_internal.h", "pass_impl.cuh"]
+HEADERS = ["rpiv_internal.h", "pass_impl.cuh", "tc_pass.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
            "--expt-relaxed-constexpr"]
@@ -39,6 +39,25 @@ def _digest() -> str:
         h.update(fh.read())
     h.update(" ".join(ARCH + NVFLAGS).encode())
     return h.hexdigest()[:16]
+
+
+FMA_SRC = "fma_peak.cu"
+FMA_LIB = os.path.join(HERE, "libfmapeak.so")
+
+
+def build_fma_peak(force: bool = False) -> str:
+    """The FP32 FMA-throughput microbenchmark (measurement support for the
+    ALU roofline), as its own small library."""
+    src = os.path.join(CSRC, FMA_SRC)
+    if not force and os.path.exists(FMA_LIB) and os.path.getmtime(FMA_LIB) >= os.path.getmtime(src):
+        return FMA_LIB
+    tmp = FMA_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([_nvcc(), *ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", src, "-o", tmp, "-lcudart"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {FMA_SRC}:\n{r.stderr}")
+    os.replace(tmp, FMA_LIB)
+    return FMA_LIB
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -200,6 +200,8 @@ struct rpiv_handle {
     std::map<std::string, cudaGraphExec_t> graphs;
     char *adj_ws = nullptr;
     size_t adj_bytes = 0;
+    float *ref_ws = nullptr;  // refinement: gu, gv, cu, cv (n floats each), score, max|g|
+    size_t ref_n = 0;
     // stage tracing
     bool tracing = false;
     struct TraceEv {
@@ -515,6 +517,37 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
 
 // ------------------------------------------------ one pass on caller scratch --
 
+namespace {
+
+// Error word of the stage entry points: bit 0 is set by a kernel whose bounded
+// wait gave up (its windows were reported invalid); rpiv_stage_status reads and
+// clears it.  A device variable, so that no call allocates for it.
+__device__ int g_stage_err;
+
+int *stage_err_word()
+{
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_stage_err) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<int *>(p);
+}
+
+// RPIV_DEBUG_STALL=1 (a tile's region wait) or 2 (a tensor-core tile's first
+// MMA wait): the stage kernels wait on a phase that nothing completes, once
+// nothing is in flight, with a short limit, so that the bounded waits and
+// their reporting can be tested without a device fault.  Read per call.
+int debug_stall()
+{
+    const char *e = std::getenv("RPIV_DEBUG_STALL");
+    if (!e) return 0;
+    const int v = std::atoi(e);
+    return (v == 1 || v == 2) ? v : 0;
+}
+
+}  // namespace
+
 size_t rpiv::single_pass_scratch_bytes(int W, int H, int R)
 {
     const int M = frame_margin(R);
@@ -599,7 +632,9 @@ int rpiv::single_pass(const void *img_a, const void *img_b, size_t pitch_bytes, 
     a.adef = ptr_direct(central ? first : nullptr, 0);
     a.def_pitch = fp;
     a.def_margin = M;
-    a.err = nullptr;
+    a.err = stage_err_word();
+    a.dbg_stall = debug_stall();
+    a.spin = a.dbg_stall ? 4096 : 0;
     a.w = window;
     a.s = step;
     a.R = radius;
@@ -964,6 +999,66 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
     return RPIV_OK;
 }
 
+rpiv_status rpiv_refine(rpiv_handle *h, const void *img_a, const void *img_b, size_t pitch_bytes, float *u, float *v,
+                        int steps, float eta0, int halvings, float *hist, void *cuda_stream)
+{
+    if (!h || !img_a || !img_b || !u || !v) return fail(RPIV_ERR_INVALID_ARG, "null argument");
+    if (steps < 0 || halvings < 0 || !(eta0 > 0.f)) return fail(RPIV_ERR_INVALID_ARG, "steps, halvings >= 0, eta0 > 0");
+    DeviceGuard dg(h->device);
+    const StageDef &d = h->stages[h->cfg.predictor_levels];
+    const size_t n = (size_t)d.nx * d.ny;
+    if (h->ref_n < n) {
+        if (h->ref_ws) {
+            cudaDeviceSynchronize();
+            cudaFree(h->ref_ws);
+            h->ref_ws = nullptr;
+            h->ref_n = 0;
+        }
+        if (cudaMalloc(&h->ref_ws, sizeof(float) * (4 * n + 64)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RPIV_ERR_OOM, "refinement buffers allocation failed");
+        }
+        h->ref_n = n;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    float *gu = h->ref_ws, *gv = gu + n, *cu = gv + n, *cv = cu + n, *dS = cv + n, *dgmax = dS + 32;
+    auto read = [&](const float *src, float *dst) -> rpiv_status {
+        CK(cudaMemcpyAsync(dst, src, sizeof(float), cudaMemcpyDeviceToHost, st), "score read");
+        CK(cudaStreamSynchronize(st), "score read");
+        return RPIV_OK;
+    };
+    rpiv_status rs;
+    float S = 0.f, gmax = 0.f;
+    if ((rs = rpiv_backward(h, img_a, img_b, pitch_bytes, u, v, 1.0f, gu, gv, dS, cuda_stream)) != RPIV_OK) return rs;
+    CK(launch_refine_absmax(gu, gv, (int)n, dgmax, st), "gradient maximum launch");
+    if ((rs = read(dS, &S)) != RPIV_OK || (rs = read(dgmax, &gmax)) != RPIV_OK) return rs;
+    if (hist) hist[0] = S;
+    for (int k = 0; k < steps; ++k) {
+        if (gmax > 0.f) {
+            double eta = (double)eta0 * std::ldexp(1.0, -k) / (double)gmax;
+            for (int t = 0; t <= halvings; ++t, eta *= 0.5) {
+                CK(launch_refine_axpy(u, v, gu, gv, (float)eta, cu, cv, (int)n, st), "step launch");
+                if ((rs = rpiv_backward(h, img_a, img_b, pitch_bytes, cu, cv, 1.0f, nullptr, nullptr, dS,
+                                        cuda_stream)) != RPIV_OK)
+                    return rs;
+                float Sc = 0.f;
+                if ((rs = read(dS, &Sc)) != RPIV_OK) return rs;
+                if (Sc > S) {
+                    CK(cudaMemcpyAsync(u, cu, sizeof(float) * n, cudaMemcpyDeviceToDevice, st), "step copy");
+                    CK(cudaMemcpyAsync(v, cv, sizeof(float) * n, cudaMemcpyDeviceToDevice, st), "step copy");
+                    break;
+                }
+            }
+        }
+        if ((rs = rpiv_backward(h, img_a, img_b, pitch_bytes, u, v, 1.0f, gu, gv, dS, cuda_stream)) != RPIV_OK)
+            return rs;
+        if ((rs = read(dS, &S)) != RPIV_OK) return rs;
+        if (hist) hist[k + 1] = S;
+    }
+    g_err.clear();
+    return RPIV_OK;
+}
+
 rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms)
 {
     if (!h) return fail(RPIV_ERR_INVALID_ARG, "handle is NULL");
@@ -991,6 +1086,31 @@ rpiv_status rpiv_wait(rpiv_handle *h, int timeout_ms)
         if (ms.count() >= timeout_ms) return fail(RPIV_ERR_TIMEOUT, "work did not finish within the timeout");
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
+}
+
+rpiv_status rpiv_stage_status(void *cuda_stream, int timeout_ms)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "stream query");
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if (ms.count() >= timeout_ms) return fail(RPIV_ERR_TIMEOUT, "stage work did not finish within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    int err = 0;
+    const int zero = 0;
+    CK(cudaMemcpyFromSymbolAsync(&err, g_stage_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st), "error word read");
+    CK(cudaStreamSynchronize(st), "error word read");
+    if (err) {
+        CK(cudaMemcpyToSymbolAsync(g_stage_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st), "error word reset");
+        CK(cudaStreamSynchronize(st), "error word reset");
+        return fail(RPIV_ERR_TIMEOUT, "a stage kernel's bounded wait gave up; its windows were reported invalid");
+    }
+    g_err.clear();
+    return RPIV_OK;
 }
 
 rpiv_status rpiv_trace_enable(rpiv_handle *h, int enable)
@@ -1054,6 +1174,7 @@ rpiv_status rpiv_destroy(rpiv_handle *h)
         if (h->fork_ev) cudaEventDestroy(h->fork_ev);
         if (h->ws) cudaFree(h->ws);
         if (h->err_dev) cudaFree(h->err_dev);
+        if (h->ref_ws) cudaFree(h->ref_ws);
         if (h->io_dev) cudaFree(h->io_dev);
         if (h->ring) cudaFreeHost(h->ring);
         if (h->adj_ws) cudaFree(h->adj_ws);

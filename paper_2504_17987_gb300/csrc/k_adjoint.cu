@@ -233,6 +233,51 @@ cudaError_t run(const AdjArgs &a, cudaStream_t st)
 
 }  // namespace
 
+// ------------------------------------------------ refinement step helpers --
+
+namespace {
+
+// cu = u + eta gu, cv = v + eta gv (FP32, one element per thread)
+__global__ void refine_axpy_kernel(const float *u, const float *v, const float *gu, const float *gv, float eta,
+                                   float *cu, float *cv, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cu[i] = fmaf(eta, gu[i], u[i]);
+    cv[i] = fmaf(eta, gv[i], v[i]);
+}
+
+// out = max(|a|, |b|) over n elements: one CTA, fixed order (max is exact)
+__global__ void refine_absmax_kernel(const float *a, const float *b, int n, float *out)
+{
+    __shared__ float part[32];
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fmaxf(fabsf(a[i]), fabsf(b[i])));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) *out = m;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_refine_axpy(const float *u, const float *v, const float *gu, const float *gv, float eta, float *cu,
+                               float *cv, int n, cudaStream_t st)
+{
+    refine_axpy_kernel<<<(n + 255) / 256, 256, 0, st>>>(u, v, gu, gv, eta, cu, cv, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_absmax(const float *a, const float *b, int n, float *out, cudaStream_t st)
+{
+    refine_absmax_kernel<<<1, 1024, 0, st>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+
 size_t adjoint_workspace_bytes(int W, int H, int nx, int ny)
 {
     return sizeof(float) * (8ull * nx * ny + 2ull * W * H) + 256;

@@ -301,7 +301,7 @@ cudaError_t launch_deform(const DeformArgs &a, int n_pairs, cudaStream_t st)
 {
     const long long WE = a.W + 2LL * a.M, HE = a.H + 2LL * a.M;
     const long long tall = ((WE + DTX - 1) / DTX) * ((HE + DTY_MAX - 1) / DTY_MAX) * n_pairs;
-    if (tall >= 2LL * 152 * 5) launch_tiles<DTY_MAX>(a, n_pairs, st);
+    if (tall >= 2LL * device_sm_count() * 5) launch_tiles<DTY_MAX>(a, n_pairs, st);
     else launch_tiles<64>(a, n_pairs, st);
     return cudaGetLastError();
 }

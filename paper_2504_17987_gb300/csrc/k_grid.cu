@@ -284,7 +284,7 @@ __global__ void ema_kernel(const float *__restrict__ x, float *state, size_t n, 
 cudaError_t launch_ema(const float *x, float *state, size_t n, float alpha, int init, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 8);
+    const size_t blocks = std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 8);
     ema_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, state, n, alpha, init);
     return cudaGetLastError();
 }

@@ -12,8 +12,8 @@
 // ingest and deformation kernels write every element the correlation kernel
 // later uses.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -23,12 +23,8 @@
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices] = {};
 
 rpiv_status bad(rpiv_status st, const char *msg)
 {
@@ -36,27 +32,34 @@ rpiv_status bad(rpiv_status st, const char *msg)
     return st;
 }
 
-// Device address of the array on the current device, looked up once per
-// device (the host-side name of a __device__ variable is not its address).
+// Device address of the array on the current device.  The host-side name of
+// a __device__ variable is not its address, so it is looked up; the lookup is
+// made on every call (it allocates nothing once the library's module is
+// loaded on the device, which the first call does), so that an address can
+// never outlive the context it belongs to.
 rpiv_status scratch_address(void **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return bad(RPIV_ERR_NO_DEVICE, "no current CUDA device");
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            char msg[160];
-            std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the static scratch failed: %s",
-                          cudaGetErrorString(e));
-            return bad(RPIV_ERR_CUDA, msg);
-        }
-        g_scratch_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        char msg[160];
+        std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the static scratch failed: %s",
+                      cudaGetErrorString(e));
+        return bad(e == cudaErrorNoDevice ? RPIV_ERR_NO_DEVICE : RPIV_ERR_CUDA, msg);
     }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return RPIV_OK;
+}
+
+// RPIV_POISON_SCRATCH=1 (testing aid): the part of the array a call uses is
+// filled with 0xFF bytes (NaN as float) on the caller's stream first, so that
+// a read of an element the call did not write surfaces instead of finding a
+// finite value left by an earlier call.  A memset, not an allocation.
+bool poison_scratch()
+{
+    const char *e = std::getenv("RPIV_POISON_SCRATCH");
+    return e && std::strcmp(e, "1") == 0;
 }
 
 }  // namespace
@@ -81,6 +84,13 @@ extern "C" rpiv_status rpiv_stage_correlate_noalloc(const void *img_a, const voi
     void *scratch = nullptr;
     rpiv_status st1 = scratch_address(&scratch);
     if (st1 != RPIV_OK) return st1;
+    if (poison_scratch()) {
+        const cudaError_t e = cudaMemsetAsync(scratch, 0xFF, need, static_cast<cudaStream_t>(cuda_stream));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bad(RPIV_ERR_CUDA, "static scratch fill failed");
+        }
+    }
     return (rpiv_status)rpiv::single_pass(img_a, img_b, pitch_bytes, fmt, width, height, window, step, radius,
                                           (int)precision, (int)deform_mode, pred_u, pred_v, u, v, info, scratch,
                                           static_cast<cudaStream_t>(cuda_stream));

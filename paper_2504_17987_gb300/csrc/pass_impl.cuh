@@ -173,12 +173,26 @@ static __device__ __forceinline__ bool load_regions(const PassArgs &a, const Til
         __syncwarp();
         for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
         for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
-        const uint32_t parity = (uint32_t)step & 1u;
-        for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
-            if (mbar_try_wait(bar, parity)) return true;
+        uint32_t parity = (uint32_t)step & 1u;
+        const int lim = a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT;
+        bool landed = false;
+        for (int it = 0; it < lim && !landed; ++it) landed = mbar_try_wait(bar, parity);
+        if (landed && a.dbg_stall == 1) {
+            // test hook: every copy has landed; the next phase expects bytes
+            // that nothing sends, so the wait below runs out with nothing in flight
+            __syncwarp();
+            if (lane == 0) mbar_expect_tx(bar, 16);
+            __syncwarp();
+            parity ^= 1u;
+            landed = false;
+            for (int it = 0; it < lim && !landed; ++it) landed = mbar_try_wait(bar, parity);
+            if (!landed && lane == 0 && a.err) atomicOr(a.err, 1);
+            return false;
+        }
+        if (landed) return true;
         if (lane == 0 && a.err) atomicOr(a.err, 1);
         // give copies still in flight a bounded chance to land before the CTA exits
-        for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+        for (int it = 0; it < lim; ++it)
             if (mbar_try_wait(bar, parity)) break;
         return false;
     }
@@ -242,10 +256,11 @@ static __device__ __forceinline__ void issue_regions(const PassArgs &a, const Ti
 static __device__ __forceinline__ bool wait_regions(const PassArgs &a, uint64_t *bar, int step)
 {
     const uint32_t parity = (uint32_t)step & 1u;
-    for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+    const int lim = a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT;
+    for (int it = 0; it < lim; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     if ((threadIdx.x & 31) == 0 && a.err) atomicOr(a.err, 1);
-    for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+    for (int it = 0; it < lim; ++it)
         if (mbar_try_wait(bar, parity)) break;
     return false;
 }
@@ -254,10 +269,12 @@ static __device__ __forceinline__ bool wait_regions(const PassArgs &a, uint64_t 
 // the slab layout, and B' twice, the second shifted one column left (TB1[x] =
 // B'[x + 1]) so that every column pair of a fragment starts 4-byte aligned,
 // with zeros wherever fragments reach outside the staged region.  A thread
-// keeps one column pair and walks rows.
+// keeps one column pair and walks rows.  Both frames are rounded with the
+// tile offset m subtracted (restored in FP32 by plane_and_peak), which keeps
+// the rounded values small.
 template <int PREC>
 __device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, const float *As, const float *Bs, uint16_t *TA,
-                          uint16_t *TB)
+                          uint16_t *TB, float m)
 {
     const PassPlan &P = a.plan;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -279,7 +296,7 @@ __device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, 
             uint32_t v = 0u;
             if (r < rows) {
                 const float2 f = *reinterpret_cast<const float2 *>(src + (j * rows + r) * P.a_pitch);
-                v = pack2<PREC>(f.x, f.y);
+                v = pack2<PREC>(f.x - m, f.y - m);
             }
             dst[(lead + u) * hpa] = v;
             r += step;
@@ -303,7 +320,7 @@ __device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, 
         const float *br = Bs + ph * P.b_pitch + x;
         uint32_t *d0 = TB0 + ph * hpb + x2, *d1 = TB1 + ph * hpb + x2;
         for (int y = ph; y < g.BR; y += step) {
-            const float v0 = k0 ? br[0] : 0.f, v1 = k1 ? br[1] : 0.f, v2 = k2 ? br[2] : 0.f;
+            const float v0 = k0 ? br[0] - m : 0.f, v1 = k1 ? br[1] - m : 0.f, v2 = k2 ? br[2] - m : 0.f;
             *d0 = pack2<PREC>(v0, v1);
             *d1 = pack2<PREC>(v1, v2);
             br += step * P.b_pitch;
@@ -865,7 +882,8 @@ struct WinShared {
 // (ring_wy + yy) & 1.
 template <int RC, bool ONE_PLANE>
 static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
-                                      const float *stats, bool tc, const WinShared &ws, int ring_wy = -1)
+                                      const float *stats, bool tc, const WinShared &ws, int ring_wy = -1,
+                                      float moff = 0.f)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -897,6 +915,12 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
         }
         return num;
     };
+    // tensor-core planes are sums of (A - m)(B' - m): the numerator of the
+    // definition is P - (mu_A - m)(S1 - n m)
+    const float nm = (float)(g.w * g.w) * moff;
+    auto coef = [&](float num, float muA, float S1, float nB) {
+        return tc ? (num - (muA - moff) * (S1 - nm)) * nB + 0.f : scaled_zncc(num, muA, S1, nB);
+    };
     for (Walk2D wk(warp, nwarps, g.nwx); wk.y < g.nwy; wk.next()) {
         const int wxi = wk.x, wyi = wk.y, wi = wyi * g.nwx + wxi;
         const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
@@ -923,12 +947,12 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
 #pragma unroll
             for (int j = 0; j < NQ; ++j) {
                 if (j < NQ - 1 || lane + 32 * j < NP)
-                    offer(scaled_zncc(block_sum(pb, qv[j]), muA, v1[vv[j]], vn[vv[j]]), qv[j]);
+                    offer(coef(block_sum(pb, qv[j]), muA, v1[vv[j]], vn[vv[j]]), qv[j]);
             }
         } else {
             for (int q = lane; q < NP; q += 32) {
                 const int qy = q / ND, vo = (qy - R) * cp + (q - qy * ND - R);
-                offer(scaled_zncc(block_sum(pb, q), muA, v1[vo], vn[vo]), q);
+                offer(coef(block_sum(pb, q), muA, v1[vo], vn[vo]), q);
             }
         }
         const uint32_t key = bq == NONE ? 0u : ord_key(best);
@@ -1246,9 +1270,22 @@ __global__ void __launch_bounds__(PASS_THREADS,
     box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
     __syncthreads();
     window_stats(a, g, bst, stats);
+    float moff = 0.f;
     if (PREC != PREC_FP32) {
+        // tile offset: the mean of the A region, from the block sums in a fixed
+        // order (kept after the region loads' barrier)
+        float *off_slot = reinterpret_cast<float *>(bar + 1);
+        if ((threadIdx.x >> 5) == 0) {
+            const int lane = threadIdx.x & 31;
+            float sum = 0.f;
+            for (int b = lane; b < g.nb; b += 32) sum += bst[b].x;
+            sum = warp_sum(sum);
+            if (lane == 0) *off_slot = sum / (float)(g.aw * g.ah);
+        }
+        __syncthreads();
+        moff = *off_slot;
         // 16-bit copies of the regions for the tensor cores, over the dead C region
-        tc_copies<PREC>(a, g, As, Bs, TA, TB);
+        tc_copies<PREC>(a, g, As, Bs, TA, TB, moff);
         __syncthreads();
     }
 
@@ -1275,7 +1312,7 @@ __global__ void __launch_bounds__(PASS_THREADS,
     if (PREC == PREC_FP32 && RC >= 0 && g.nwin >= 2 * (int)(blockDim.x >> 5))
         plane_and_peak_pairs<(RC >= 0 ? RC : 0)>(a, g, Ps, Vs, stats, ws);
     else
-        plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws);
+        plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws, -1, moff);
     __syncthreads();
     stencil_direct(a, g, As, Bs, ws);
     __syncthreads();

@@ -17,6 +17,20 @@ void prepare_pass_fp32();
 void prepare_pass_bf16();
 void prepare_pass_fp16();
 
+int device_sm_count()
+{
+    constexpr int kMaxDev = 64;
+    static int count[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+    if (!count[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+        count[dev] = n;
+    }
+    return count[dev];
+}
+
 void prepare_pass_kernels()
 {
     static int prepared_device = -1;
@@ -213,7 +227,77 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool str
     return L;
 }
 
+// Tensor-core (tcgen05) tiles: 50 % overlap (w = 2s, s a multiple of 8) at
+// r = 4.  The FP32 regions, box sums and statistics are laid out as for the
+// FP32 kernel; the planes are one NP-float plane per window, kept for the whole
+// tile; the dead column box sums hold, per window row, the zero-banded A slab,
+// a ring of nbuf buffers of shifted B' copies (one MMA group of 4 rows each)
+// and the epilogue buffer, and later the per-window stencil buffers.  The MMAs
+// of a copy buffer read up to 2048 - (2R + 1) 64 bytes past its last chunk
+// (the unused shift slots of the last chunks), which the epilogue buffer after
+// the ring covers.
+constexpr int kTcRows = 4;
+constexpr int kTcEbufBytes = 4 * 32 * 20 * 4;
+
+bool tc_shape(int w, int s, int R) { return R == 4 && w == 2 * s && (s == 8 || s == 16 || s == 32); }
+
+Layout layout_for_tc(int TX, int TY, int w, int s, int R, int nbuf)
+{
+    Layout L = layout_for(TX, TY, w, s, R, s, PREC_FP32);
+    PassPlan &p = L.p;
+    const int ND = 2 * R + 1, NP = ND * ND;
+    const int aw = (TX - 1) * s + w, ah = (TY - 1) * s + w;
+    const int BR = ah + 2 * (R + 1), vh = BR - w + 1;
+    const int nwin = TX * TY, nch = aw / 8, ng = (w + 2 * R) / kTcRows;
+    p.RGx = 1;
+    p.pstride = NP;
+    p.tc = 1;
+    p.slab_rows = w + 2 * R + 16 - kTcRows;
+    p.slab_lbo = p.slab_rows * 16;
+    p.cp_lbo = ND * kTcRows * 16;
+    p.cp_bytes = nch * p.cp_lbo;
+    p.tc_nbuf = std::max(2, std::min(nbuf, ng));
+    int cols = 32;
+    while (cols < 16 * TX) cols *= 2;
+    p.tmem_cols = cols;
+    // rebuild the offsets past the box sums: [stats][mbarriers][block stats][planes][reused region]
+    int off = p.off_v + up(2 * vh * p.v_pitch * 4, 16);
+    auto take = [&](int bytes) {
+        int o = off;
+        off = up(off + bytes, 16);
+        return o;
+    };
+    p.off_stats = take(2 * nwin * 4);
+    p.off_red = take(8 * (1 + p.tc_nbuf) + 8);  // barriers, then the TMEM address and the tile offset
+    p.off_gst = take((aw / s) * (ah / s) * 8);
+    p.off_p = take(nwin * NP * 4);
+    p.off_h = off;
+    const int c_bytes = 2 * vh * p.h_pitch * 4;
+    p.off_slab = off;
+    p.off_cp = up(p.off_slab + nch * p.slab_lbo, 16);
+    p.off_ebuf = up(p.off_cp + p.tc_nbuf * p.cp_bytes, 16);
+    const int tc_end = p.off_ebuf + kTcEbufBytes;
+    const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(std::max(nwin, kThreads / 32) * 5 * 4, 16);
+    p.off_c5 = off;
+    p.off_peaks = p.off_c5 + up(nwin * 5 * 4, 16);
+    p.off_need = p.off_peaks + up(nwin * 4, 16);
+    p.off_dpart = p.off_need + up(nwin * 4, 16);
+    off = std::max({off + c_bytes, tc_end, off + win_bytes});
+    p.smem_bytes = up(off, 16);
+    p.max_windows = nwin;
+    L.bytes = p.smem_bytes;
+    return L;
+}
+
 }  // namespace
+
+// RPIV_TC_PLANES=0 keeps the mma.sync planes for the shapes the tcgen05
+// kernel covers (tests run both); read at each plan.
+bool tc_planes_enabled()
+{
+    const char *e = std::getenv("RPIV_TC_PLANES");
+    return !(e && std::strcmp(e, "0") == 0);
+}
 
 bool pass_supported(int R, int prec)
 {
@@ -340,9 +424,47 @@ bool plan_strip(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *
     return true;
 }
 
+// Tensor-core tiles: among shapes of up to 8 x 8 windows that leave room for
+// two CTAs per SM (shared memory, and 512 TMEM columns per SM), the one with
+// the most windows, then the fewest copy buffers' bytes; copy rings of two
+// buffers, or one per MMA group of a window row when that fits.
+bool plan_tc(int w, int s, int R, int nx, int ny, PassPlan *plan)
+{
+    const int target = 2;
+    const int ng = (w + 2 * R) / kTcRows;
+    double best = -1e30;
+    Layout pick{};
+    int pick_tx = 0, pick_ty = 0;
+    for (int ty = 1; ty <= std::min(8, ny); ++ty)
+        for (int tx = 1; tx <= std::min(8, nx); ++tx)
+            for (int nbuf : {ng, 2}) {
+                Layout L = layout_for_tc(tx, ty, w, s, R, nbuf);
+                if (L.bytes > kSmemMax) continue;
+                const int ctas = std::min({228 * 1024 / (L.bytes + 1024), 2048 / kThreads, 512 / L.p.tmem_cols});
+                if (ctas < 1) continue;
+                const double score = std::min(ctas, target) * 1e8 + (double)tx * ty * 1e5 +
+                                     (L.p.tc_nbuf >= ng ? 1e3 : 0) - std::abs(tx - ty);
+                if (score > best) {
+                    best = score;
+                    pick = L;
+                    pick_tx = tx;
+                    pick_ty = ty;
+                }
+            }
+    if (pick_tx == 0) return false;
+    *plan = pick.p;
+    plan->tiles_x = (nx + pick_tx - 1) / pick_tx;
+    plan->tiles_y = (ny + pick_ty - 1) / pick_ty;
+    return true;
+}
+
 bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan, PassPlan *strip)
 {
     if (w < 2 || s < 1 || nx < 1 || ny < 1 || !pass_supported(R, prec)) return false;
+    if (prec != PREC_FP32 && tc_shape(w, s, R) && tc_planes_enabled()) {
+        if (strip) std::memset(strip, 0, sizeof(*strip));
+        return plan_tc(w, s, R, nx, ny, plan);
+    }
     const int G = gcd(w, s);
     if (prec != PREC_FP32 && (G % 2) != 0) return false;  // paired 16-bit loads need even blocks
     if (strip) {
@@ -353,11 +475,9 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan, Pa
 }
 
 // A strip launch walks its segments serially inside each CTA, so it is taken
-// only when the batch gives it about four waves of CTAs (three per SM).
-// RPIV_STRIP_MIN_CTAS overrides the threshold (tuning, and the tests that run
-// both forms); it is read at each launch.
-constexpr long long kStripMinCtas = 4LL * 152 * 3;
-
+// only when the batch gives it about four waves of CTAs (three per SM of the
+// device).  RPIV_STRIP_MIN_CTAS overrides the threshold (tuning, and the
+// tests that run both forms); it is read at each launch.
 long long strip_min_ctas()
 {
     const char *e = std::getenv("RPIV_STRIP_MIN_CTAS");
@@ -365,7 +485,7 @@ long long strip_min_ctas()
         const long long v = std::atoll(e);
         if (v >= 1) return v;
     }
-    return kStripMinCtas;
+    return 4LL * device_sm_count() * 3;
 }
 
 cudaError_t launch_pass(const PassArgs &args_in, int n_pairs, cudaStream_t st)

@@ -87,6 +87,13 @@ struct PassPlan {
     int off_gst;                 // per-G x G block sum and centred sum of squares of A
     int off_c5, off_peaks, off_need, off_dpart;  // per-window stencil values, argmax, direct-sum mask and sums
     int max_windows, max_blocks;
+    // tcgen05 planes (tc = 1; BF16/FP16, 50 % overlap, r = 4): per window row a
+    // zero-banded A slab, a ring of tc_nbuf buffers of shifted B' copies (one
+    // MMA group of rows each), an epilogue buffer, tmem_cols TMEM columns
+    int tc;
+    int off_slab, slab_rows, slab_lbo;  // bytes; slab_lbo: stride of its 8-column chunks
+    int off_cp, cp_bytes, cp_lbo, tc_nbuf;  // copy buffers: cp_bytes each, chunk stride cp_lbo
+    int off_ebuf, tmem_cols;
 };
 
 struct PassArgs {
@@ -99,6 +106,9 @@ struct PassArgs {
     long long def_pitch;   // floats between rows of afl / bdef / adef (a multiple of 32)
     int def_margin;        // a multiple of 4, at least R + 1
     int *err;              // nullable: bit 0 set if a bounded wait gave up
+    int spin;              // polls of a bounded wait (0: the default limit)
+    int dbg_stall;         // test hook: 1 a tile's region wait, 2 its first MMA wait (tensor-core
+                           // tiles) waits on a phase nothing completes, once nothing is in flight
     int w, s, R, nx, ny;
     int deform;            // 0: frame B only, 1: central
     int prec;
@@ -124,6 +134,10 @@ struct DeformArgs {
 };
 cudaError_t launch_deform(const DeformArgs &a, int n_pairs, cudaStream_t st);
 bool deform_nodes_fit(int w, int s, int nx, int ny);
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device); launch shapes that fill the device scale with it.
+int device_sm_count();
 
 // Opts every pass-kernel instantiation in to the full shared-memory carve-out
 // on the current device (once per device; never inside a stream capture).
@@ -246,5 +260,9 @@ struct AdjArgs {
 };
 size_t adjoint_workspace_bytes(int W, int H, int nx, int ny);
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t st);
+// Refinement step helpers: cu = u + eta gu (and v), and max(|a|, |b|) into *out.
+cudaError_t launch_refine_axpy(const float *u, const float *v, const float *gu, const float *gv, float eta, float *cu,
+                               float *cv, int n, cudaStream_t st);
+cudaError_t launch_refine_absmax(const float *a, const float *b, int n, float *out, cudaStream_t st);
 
 }  // namespace rpiv

@@ -1,0 +1,491 @@
+// Correlation pass with the planes on the fifth-generation tensor cores
+// (tcgen05, accumulators in tensor memory), for 50 % overlap (w = 2s, s a
+// multiple of 8) at r = 4 (paper Sec. 2: correlation coefficients of the
+// warped pair; here BF16 or FP16 products with FP32 accumulation choose the
+// integer peak, and the five-point stencil of the Gaussian fit is refitted in
+// FP32 from the FP32 frames).
+//
+// The contraction.  For one window, a group of TC_ROWS consecutive rows r of
+// B' and the A rows that meet them (a zero-banded slab, so that rows outside
+// the window contribute nothing), one MMA of M = 128, N = 16, K = 16 computes
+//     D[(c, i)][n] = sum_k B'(r0 + i, x0 + k + c - R) (A(a0 + n, x0 + k) - m)
+// with M = (shift slot c, row i): 32 slots of TC_ROWS rows, the slots c <= 2R
+// being shifted copies of B' (sx = c - R), N = 16 A rows, K = 16 columns of
+// the window.  Since sy = r0 + i - (a0 + n) = i + R - n for every group, the
+// groups of a window accumulate into one TMEM block of 16 columns, and
+//     P_w(sy, sx) = sum_i D[(sx + R, i)][i + R - sy]
+// is a four-term diagonal sum in the epilogue.  m is a per-tile offset
+// subtracted from both frames before rounding to 16 bits (it is restored
+// exactly in FP32 from the window and box sums), which keeps the rounded
+// operands small.
+//
+// Layouts (canonical K-major, no swizzle: 8 rows of 16 bytes per core matrix):
+//   copies  per chunk q of 8 columns: slots c = 0..2R, each TC_ROWS rows of 16 B;
+//           the M index m = TC_ROWS c + i is linear at 16 B (SBO = 128), the
+//           chunk stride (LBO) is (2R + 1) TC_ROWS 16 B, so the unused slots
+//           c > 2R of a chunk read the following chunks (their D rows are never
+//           read)
+//   slab    per chunk q: the window row's A rows from 2R above the window to
+//           16 - TC_ROWS below it, rows of 16 B (SBO = 128), chunk stride LBO
+// Window rows of the tile are processed in turn; a group's copies are staged
+// in a ring of buffers, each released by the commit of the MMAs that read it.
+#pragma once
+
+#include "pass_impl.cuh"
+
+namespace rpiv {
+
+constexpr int TC_ROWS = 4;    // B' rows per MMA group
+constexpr int TC_M = 128;     // 32 shift slots x TC_ROWS rows
+constexpr int TC_N = 16;      // A rows of a group
+constexpr int TC_R = 4;       // the radius these kernels are built for
+constexpr int TC_EB_PITCH = 20;  // floats per lane in the epilogue buffer (conflict-free 128-bit stores)
+
+static_assert(TC_ROWS + 2 * TC_R <= TC_N, "a group's A rows must fit N");
+
+// ------------------------------------------------ tcgen05 building blocks --
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, each >> 4 in 14 bits; bit 46 = descriptor version of this family;
+// no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B both BF16 (or
+// both F16), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <int PREC>
+__device__ __forceinline__ uint32_t tc_idesc()
+{
+    constexpr uint32_t f = PREC == PREC_BF16 ? 1u : 0u;
+    return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// arrive on bar once every MMA this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 16 columns of FP32 from tensor memory (the warp's lane quarter)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// whole warp: allocate cols columns (power of two >= 32); the address lands in *slot
+__device__ __forceinline__ void tc_alloc(uint32_t *slot, int cols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, int cols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+// Warp 0 polls phase `parity` of bar (bounded); every thread returns the same
+// verdict.  On timeout the error word is set.
+static __device__ __forceinline__ bool tc_cta_wait(const PassArgs &a, uint64_t *bar, uint32_t parity)
+{
+    bool ok = true;
+    if (threadIdx.x < 32) {
+        ok = false;
+        const int lim = a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT;
+        for (int it = 0; it < lim; ++it)
+            if (mbar_try_wait(bar, parity)) {
+                ok = true;
+                break;
+            }
+        if (!ok && threadIdx.x == 0 && a.err) atomicOr(a.err, 1);
+    }
+    return !__syncthreads_or(!ok);
+}
+
+// ------------------------------------------------------ operand staging --
+
+template <int PREC>
+__device__ __forceinline__ uint4 pack8(float4 lo, float4 hi, float m)
+{
+    uint4 r;
+    r.x = pack2<PREC>(lo.x - m, lo.y - m);
+    r.y = pack2<PREC>(lo.z - m, lo.w - m);
+    r.z = pack2<PREC>(hi.x - m, hi.y - m);
+    r.w = pack2<PREC>(hi.z - m, hi.w - m);
+    return r;
+}
+
+// Slab of window row wy: slab row j holds A row wy s - 2R + j (tile rows),
+// minus m, where it lies in the window; zero elsewhere.
+template <int PREC>
+static __device__ __forceinline__ void tc_build_slab(const PassPlan &P, const TileGeom &g, const float *As,
+                                                     unsigned char *slab, int wy, float m)
+{
+    const int rows = P.slab_rows, nch = g.aw >> 3;
+    for (int it = threadIdx.x; it < rows * nch; it += blockDim.x) {
+        const int q = it / rows, j = it - q * rows;
+        const int r = j - 2 * TC_R;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r >= 0 && r < g.w) {
+            const float *src = As + (wy * g.s + r) * P.a_pitch + 8 * q;
+            v = pack8<PREC>(*reinterpret_cast<const float4 *>(src), *reinterpret_cast<const float4 *>(src + 4), m);
+        }
+        *reinterpret_cast<uint4 *>(slab + q * P.slab_lbo + j * 16) = v;
+    }
+}
+
+// Shifted copies of group gi of window row wy: B' rows y = wy s - R + TC_ROWS gi
+// + i (tile rows); slot c, chunk q, row i holds B'(y, 8q + t + c - R) - m.
+// A thread takes one (row, chunk): 16 floats, the even and odd column pairs
+// converted once, 2R + 1 stores of 16 bytes.
+template <int PREC>
+static __device__ __forceinline__ void tc_build_group(const PassPlan &P, const TileGeom &g, const float *Bs,
+                                                      unsigned char *buf, int wy, int gi, float m)
+{
+    constexpr int R = TC_R;
+    const int nch = g.aw >> 3;
+    for (int it = threadIdx.x; it < TC_ROWS * nch; it += blockDim.x) {
+        const int q = it / TC_ROWS, i = it - q * TC_ROWS;
+        const int y = wy * g.s - R + TC_ROWS * gi + i;
+        const float *src = Bs + (y + R + 1) * P.b_pitch + P.padl + 8 * q - R;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 f = *reinterpret_cast<const float4 *>(src + 4 * j);
+            v[4 * j] = f.x - m;
+            v[4 * j + 1] = f.y - m;
+            v[4 * j + 2] = f.z - m;
+            v[4 * j + 3] = f.w - m;
+        }
+        uint32_t ev[8], od[7];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ev[j] = pack2<PREC>(v[2 * j], v[2 * j + 1]);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) od[j] = pack2<PREC>(v[2 * j + 1], v[2 * j + 2]);
+        unsigned char *dst = buf + q * P.cp_lbo + i * 16;
+#pragma unroll
+        for (int c = 0; c <= 2 * R; ++c) {
+            uint4 wv;
+            if ((c & 1) == 0)
+                wv = make_uint4(ev[c / 2], ev[c / 2 + 1], ev[c / 2 + 2], ev[c / 2 + 3]);
+            else
+                wv = make_uint4(od[c / 2], od[c / 2 + 1], od[c / 2 + 2], od[c / 2 + 3]);
+            *reinterpret_cast<uint4 *>(dst + c * (TC_ROWS * 16)) = wv;
+        }
+    }
+}
+
+// ------------------------------------------------------------- epilogue --
+
+// Window wx of row wy: warps of lane quarter 0 (slots 0..7) and 1 (slot 8)
+// read the window's 16 TMEM columns, stage them per lane, and form the
+// diagonal sums P_w(sy, sx) into the plane buffer.
+static __device__ __forceinline__ void tc_epilogue(const TileGeom &g, uint32_t tmem, float *ebuf, float *Ps, int wy)
+{
+    constexpr int R = TC_R, ND = 2 * R + 1, NP = ND * ND;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, half = warp >> 2, nhalf = blockDim.x >> 7;
+    if (quarter >= 2) return;
+    float *eb = ebuf + (half * 2 + quarter) * 32 * TC_EB_PITCH;
+    const int nout = quarter == 0 ? 8 * ND : ND;  // slots 0..7, or slot 8
+    for (int wx = half; wx < g.nwx; wx += nhalf) {
+        float r[16];
+        tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * wx), r);
+        float4 *d4 = reinterpret_cast<float4 *>(eb + lane * TC_EB_PITCH);
+        d4[0] = make_float4(r[0], r[1], r[2], r[3]);
+        d4[1] = make_float4(r[4], r[5], r[6], r[7]);
+        d4[2] = make_float4(r[8], r[9], r[10], r[11]);
+        d4[3] = make_float4(r[12], r[13], r[14], r[15]);
+        __syncwarp();
+        float *pw = Ps + (wy * g.nwx + wx) * NP;
+        for (int o = lane; o < nout; o += 32) {
+            const int cl = o / ND, syi = o - cl * ND;  // slot 8 quarter + cl, sy = syi - R
+            // lane 4 cl + i holds row i of the slot; its column for sy is i + R - sy
+            const float *e = eb + (TC_ROWS * cl) * TC_EB_PITCH + (2 * R - syi);
+            float s = e[0];
+            s += e[TC_EB_PITCH + 1];
+            s += e[2 * TC_EB_PITCH + 2];
+            s += e[3 * TC_EB_PITCH + 3];
+            pw[syi * ND + 8 * quarter + cl] = s;
+        }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------------------- planes --
+
+// Planes of every window of the tile into Ps (NP floats per window), window
+// row by window row.  Returns false (error word set, MMAs in flight drained
+// with a bounded wait) if a wait gave up.
+template <int PREC, int GC>
+static __device__ __forceinline__ bool tc_planes(const PassArgs &a, const TileGeom &g, const float *As,
+                                                 const float *Bs, float *Ps, unsigned char *smem, uint32_t tmem,
+                                                 uint64_t *mbar, float m)
+{
+    constexpr int R = TC_R, W = 2 * GC, NG = (W + 2 * R) / TC_ROWS, KS = W / 16, CPW = GC / 8;
+    static_assert((W + 2 * R) % TC_ROWS == 0 && GC % 8 == 0, "shape");
+    const PassPlan &P = a.plan;
+    const int tid = threadIdx.x;
+    const int nbuf = P.tc_nbuf;
+    unsigned char *slab = smem + P.off_slab;
+    float *ebuf = reinterpret_cast<float *>(smem + P.off_ebuf);
+    const uint32_t slab_s = smem_addr(slab), cp_s = smem_addr(smem + P.off_cp);
+    const uint32_t idesc = tc_idesc<PREC>();
+    // per buffer: commits issued and waited (parity of the next wait = waited & 1)
+    uint32_t issued_mask = 0;  // buffers with a commit not yet waited for
+    uint32_t waited = 0;       // bit b: parity of buffer b's next wait
+    int step = 0;
+    // test hook: wait on a phase of the first buffer's barrier that no commit
+    // completes, before any MMA is issued (the wait runs out with nothing in flight)
+    if (a.dbg_stall == 2 && !tc_cta_wait(a, mbar, 0u)) goto drain;
+    for (int wy = 0; wy < g.nwy; ++wy) {
+        tc_build_slab<PREC>(P, g, As, slab, wy, m);
+        for (int gi = 0; gi < NG; ++gi, ++step) {
+            const int b = step % nbuf;
+            if (issued_mask & (1u << b)) {
+                // the MMAs that read this buffer last must have completed
+                if (!tc_cta_wait(a, mbar + b, (waited >> b) & 1u)) goto drain;
+                waited ^= 1u << b;
+                issued_mask &= ~(1u << b);
+            }
+            tc_build_group<PREC>(P, g, Bs, smem + P.off_cp + b * P.cp_bytes, wy, gi, m);
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint64_t da0 = tc_desc(cp_s + b * P.cp_bytes, P.cp_lbo, 128);
+                const uint64_t db0 = tc_desc(slab_s + TC_ROWS * gi * 16, P.slab_lbo, 128);
+                for (int wx = 0; wx < g.nwx; ++wx) {
+#pragma unroll
+                    for (int kk = 0; kk < KS; ++kk) {
+                        const int chunk = wx * CPW + 2 * kk;
+                        // the start-address field is the low 14 bits, in units of 16 bytes
+                        tc_mma(tmem + (uint32_t)(16 * wx), da0 + (uint64_t)((chunk * P.cp_lbo) >> 4),
+                               db0 + (uint64_t)((chunk * P.slab_lbo) >> 4), idesc, (gi | kk) != 0 ? 1u : 0u);
+                    }
+                }
+                tc_commit(mbar + b);
+            }
+            issued_mask |= 1u << b;
+        }
+        // every MMA of the row has completed once each pending commit has
+        for (int b = 0; b < nbuf; ++b)
+            if (issued_mask & (1u << b)) {
+                if (!tc_cta_wait(a, mbar + b, (waited >> b) & 1u)) goto drain;
+                waited ^= 1u << b;
+                issued_mask &= ~(1u << b);
+            }
+        tc_fence_after();
+        tc_epilogue(g, tmem, ebuf, Ps, wy);
+        // TMEM columns and the slab are rewritten by the next row
+        tc_fence_before();
+        __syncthreads();
+    }
+    return true;
+drain:
+    // a second bounded chance for the MMAs in flight before the caller frees TMEM
+    for (int b = 0; b < nbuf; ++b)
+        if (issued_mask & (1u << b)) {
+            if (threadIdx.x < 32)
+                for (int it = 0; it < (a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT); ++it)
+                    if (mbar_try_wait(mbar + b, (waited >> b) & 1u)) break;
+        }
+    __syncthreads();
+    return false;
+}
+
+// One warp per window: the scaled coefficient from the window's plane in
+// offset form, (P - (mu_A - m)(S1 - n m)) / sqrt(E_B), which equals the
+// numerator sum (A - mu_A) B' of the definition; argmax with ties to the
+// smallest row-major index; all five stencil points go to the FP32 refit.
+static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps,
+                                                         const float *Vs, const float *stats, float m,
+                                                         const WinShared &ws)
+{
+    constexpr int R = TC_R, ND = 2 * R + 1, NP = ND * ND, NQ = (NP + 31) / 32;
+    constexpr uint32_t NONE = 0xffffffffu;
+    const PassPlan &P = a.plan;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float n = (float)(g.w * g.w), tau = TAU_PER_PIXEL * n, nm = n * m;
+    const int cp = P.v_pitch;
+    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    int qv[NQ], vv[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const int q = min(lane + 32 * j, NP - 1);
+        const int qy = q / ND, qx = q - qy * ND;
+        qv[j] = q;
+        vv[j] = (qy - R) * cp + (qx - R);
+    }
+    for (int wi = warp; wi < g.nwin; wi += nwarps) {
+        const int wyi = wi / g.nwx, wxi = wi - wyi * g.nwx;
+        const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
+        if (!(EA > tau)) {
+            if (lane == 0) {
+                ws.peaks[wi] = NP / 2;
+                ws.need[wi] = 0;
+            }
+            continue;
+        }
+        const float dmu = muA - m;
+        const float *pw = Ps + wi * NP;
+        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        float best = 0.f;
+        uint32_t bq = NONE;
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            if (j < NQ - 1 || lane + 32 * j < NP) {
+                const float c = (pw[qv[j]] - dmu * (v1[vv[j]] - nm)) * vn[vv[j]] + 0.f;
+                // ascending q: the first of equal values stays; NaN never wins
+                if (c > best || (bq == NONE && c == c)) {
+                    best = c;
+                    bq = (uint32_t)qv[j];
+                }
+            }
+        }
+        const uint32_t key = bq == NONE ? 0u : ord_key(best);
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+        const uint32_t qmin = __reduce_min_sync(0xffffffffu, (key == kmax && bq != NONE) ? bq : NONE);
+        if (lane == 0) {
+            ws.peaks[wi] = qmin < (uint32_t)NP ? (int)qmin : NP / 2;  // no finite value: zero shift
+            ws.need[wi] = 0x1f;
+        }
+    }
+}
+
+// ------------------------------------------------------------- the kernel --
+
+// Tiles of TX x TY windows of 50 % overlap (w = 2 GC, s = GC), r = 4: regions,
+// FP32 statistics and box sums as in pass_kernel, tensor-core planes per window
+// row, argmax on the planes, FP32 five-point refit, Gaussian fit.
+template <int PREC, int GC>
+__global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const PassArgs a)
+{
+    constexpr int R = TC_R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PassPlan &P = a.plan;
+    TileGeom g;
+    g.R = R;
+    g.ND = 2 * R + 1;
+    g.NP = g.ND * g.ND;
+    g.G = GC;
+    g.w = 2 * GC;
+    g.s = GC;
+    g.kb = 2;
+    const int pair = blockIdx.z;
+    const int s = g.s, w = g.w;
+    g.wx0 = blockIdx.x * P.TX;
+    g.wy0 = blockIdx.y * P.TY;
+    g.nwx = min(P.TX, a.nx - g.wx0);
+    g.nwy = min(P.TY, a.ny - g.wy0);
+    g.nwin = g.nwx * g.nwy;
+    g.aw = (g.nwx - 1) * s + w;
+    g.ah = (g.nwy - 1) * s + w;
+    g.ax0 = g.wx0 * s;
+    g.ay0 = g.wy0 * s;
+    g.BC = g.aw + 2 * (R + 1);
+    g.BR = g.ah + 2 * (R + 1);
+    g.OFFB = P.padl - (R + 1);
+    g.hw = g.BC - w + 1;
+    g.vh = g.BR - w + 1;
+    g.nbx = g.aw / g.G;
+    g.nby = g.ah / g.G;
+    g.nb = g.nbx * g.nby;
+
+    float *As = reinterpret_cast<float *>(smem + P.off_a);
+    float *Bs = reinterpret_cast<float *>(smem + P.off_b);
+    float *Cs = reinterpret_cast<float *>(smem + P.off_h);
+    float *Vs = reinterpret_cast<float *>(smem + P.off_v);
+    float *Ps = reinterpret_cast<float *>(smem + P.off_p);
+    float *stats = reinterpret_cast<float *>(smem + P.off_stats);
+    float2 *bst = reinterpret_cast<float2 *>(smem + P.off_gst);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + P.off_red);  // [0]: regions, [1..]: MMA buffers
+    // after the barriers: the TMEM address and the tile offset (no static
+    // shared memory, so that the full dynamic carve-out can be granted)
+    uint32_t &tmem_slot = *reinterpret_cast<uint32_t *>(bar + 1 + P.tc_nbuf);
+    float &tile_off = *(reinterpret_cast<float *>(bar + 1 + P.tc_nbuf) + 1);
+    WinShared ws;
+    ws.c5 = reinterpret_cast<float *>(smem + P.off_c5);
+    ws.peaks = reinterpret_cast<int *>(smem + P.off_peaks);
+    ws.need = reinterpret_cast<int *>(smem + P.off_need);
+    ws.dpart = reinterpret_cast<float *>(smem + P.off_dpart);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // 1: A and B' regions
+    const bool loaded = load_regions(a, g, pair, As, Bs, bar);
+    if (__syncthreads_or(!loaded)) {
+        invalid_tile(a, g, pair);
+        return;
+    }
+    if (warp == 0) tc_alloc(&tmem_slot, P.tmem_cols);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < P.tc_nbuf; ++b) mbar_init(bar + 1 + b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+
+    // 2: A window statistics, box sums of B' for every window and shift
+    block_stats(a, g, As, bst);
+    box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
+    __syncthreads();
+    window_stats(a, g, bst, stats);
+    if (warp == 0) {
+        // tile offset: the mean of the A region, from the block sums in a fixed order
+        float sum = 0.f;
+        for (int b = lane; b < g.nb; b += 32) sum += bst[b].x;
+        sum = warp_sum(sum);
+        if (lane == 0) tile_off = sum / (float)(g.aw * g.ah);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const float m = tile_off;
+
+    // 3: tensor-core planes (operand buffers over the dead C region)
+    const bool ok = tc_planes<PREC, GC>(a, g, As, Bs, Ps, smem, tmem, bar + 1, m);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tmem, P.tmem_cols);
+    if (!ok) {
+        invalid_tile(a, g, pair);
+        return;
+    }
+
+    // 4: argmax on the planes, FP32 five-point refit, Gaussian fit, outputs
+    tc_plane_and_peak(a, g, Ps, Vs, stats, m, ws);
+    __syncthreads();
+    stencil_direct(a, g, As, Bs, ws);
+    __syncthreads();
+    finalize(a, g, Vs, stats, ws, pair);
+}
+
+}  // namespace rpiv

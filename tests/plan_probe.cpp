@@ -3,6 +3,8 @@
 // entry points it refers to are stubs, so no device is involved.  Reads
 // "w s R nx ny prec" lines on stdin and prints one line per case:
 //   ok TX TY tiles_x tiles_y smem RGx lv lh nv nh | sTX srows stiles_x stiles_y ssmem slv slh snv snh
+//   | tc off_p off_red off_gst off_h off_slab slab_rows slab_lbo off_cp cp_bytes cp_lbo nbuf off_ebuf tmem_cols
+//     off_c5 off_dpart
 #include <cstdio>
 
 #include "rpiv_internal.h"
@@ -24,16 +26,25 @@ extern "C" cudaError_t cudaGetDevice(int *d)
     return cudaSuccess;
 }
 
+extern "C" cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int)
+{
+    *v = 152;
+    return cudaSuccess;
+}
+
 int main()
 {
     int w, s, R, nx, ny, prec;
     while (std::scanf("%d %d %d %d %d %d", &w, &s, &R, &nx, &ny, &prec) == 6) {
         rpiv::PassPlan p{}, st{};
         const bool ok = rpiv::pass_plan(w, s, R, nx, ny, prec, &p, &st);
-        std::printf("%d %d %d %d %d %d %d %d %d %d %d | %d %d %d %d %d %d %d %d %d\n", ok ? 1 : 0, p.TX, p.TY,
+        std::printf("%d %d %d %d %d %d %d %d %d %d %d | %d %d %d %d %d %d %d %d %d", ok ? 1 : 0, p.TX, p.TY,
                     p.tiles_x, p.tiles_y, p.smem_bytes, p.RGx, p.box_lv, p.box_lh, p.box_nv, p.box_nh, st.TX,
                     st.strip_rows, st.tiles_x, st.tiles_y, st.smem_bytes, st.box_lv, st.box_lh, st.box_nv,
                     st.box_nh);
+        std::printf(" | %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", p.tc, p.off_p, p.off_red, p.off_gst,
+                    p.off_h, p.off_slab, p.slab_rows, p.slab_lbo, p.off_cp, p.cp_bytes, p.cp_lbo, p.tc_nbuf,
+                    p.off_ebuf, p.tmem_cols, p.off_c5, p.off_dpart);
     }
     return 0;
 }

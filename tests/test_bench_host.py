@@ -6,7 +6,7 @@ import shutil
 
 import bench
 
-FILES = ("pass_impl.cuh", "k_pass_fp32.cu", "k_pass_bf16.cu", "k_pass_fp16.cu", "pass_plan.cpp")
+FILES = ("pass_impl.cuh", "tc_pass.cuh", "k_pass_fp32.cu", "k_pass_tc.cu", "pass_plan.cpp")
 
 
 def _copy_sources(tmp_path):

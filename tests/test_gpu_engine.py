@@ -69,3 +69,33 @@ def test_batch_of_distinct_pairs_equals_pairs_one_by_one():
         for x, y in zip(got, single):
             assert torch.equal(x, y)
     eng.close()
+
+
+@pytest.mark.parametrize("stall,precision", [(1, "fp32"), (1, "bf16"), (2, "bf16")])
+def test_stage_bounded_wait_runs_out_and_is_reported(stall, precision, monkeypatch):
+    """A stage kernel's bounded wait made to run out (the test hook waits on a
+    barrier phase that nothing completes, after the region copies have landed
+    or before any MMA is issued): the call itself succeeds, its windows are
+    reported invalid with the predictor passed through, rpiv_stage_status
+    returns TIMEOUT once, and the next call is unaffected."""
+    from synth import workloads as wl
+    A, B = wl.paper_1mp(W=256, H=224).render()
+    a, b = rp.to_device(A, "cuda:0"), rp.to_device(B, "cuda:0")
+    nx, ny = (256 - 16) // 8 + 1, (224 - 16) // 8 + 1
+    pu = torch.full((ny, nx), 12.0, device="cuda:0")
+    pv = torch.full((ny, nx), -0.5, device="cuda:0")
+    rp.stage_status()  # start from a clear word
+    monkeypatch.setenv("RPIV_DEBUG_STALL", str(stall))
+    u, v, info = rp.stage_correlate(a, b, 16, 8, 4, pu, pv, precision=precision)
+    torch.cuda.synchronize()
+    with pytest.raises(rp.RpivError) as ei:
+        rp.stage_status()
+    assert ei.value.status == 5
+    assert int(info.count_nonzero()) == 0
+    assert torch.equal(u, pu) and torch.equal(v, pv)
+    rp.stage_status()  # read once, then clear
+    monkeypatch.delenv("RPIV_DEBUG_STALL")
+    u, v, info = rp.stage_correlate(a, b, 16, 8, 4, pu, pv, precision=precision)
+    rp.stage_status()
+    valid = rp.decode_info(info)[0]
+    assert float(valid.float().mean()) > 0.99

@@ -46,12 +46,14 @@ def probe(tmp_path_factory):
         out = subprocess.run([exe], input=text, check=True, capture_output=True, text=True, env=env).stdout
         res = []
         for line in out.strip().splitlines():
-            a, b = line.split("|")
-            t, st = [int(x) for x in a.split()], [int(x) for x in b.split()]
+            a, b, c = line.split("|")
+            t, st, tc = [int(x) for x in a.split()], [int(x) for x in b.split()], [int(x) for x in c.split()]
             res.append(dict(ok=t[0], TX=t[1], TY=t[2], tiles_x=t[3], tiles_y=t[4], smem=t[5], RG=t[6], lv=t[7],
                             lh=t[8], nv=t[9], nh=t[10],
                             strip=dict(TX=st[0], rows=st[1], tiles_x=st[2], tiles_y=st[3], smem=st[4], lv=st[5],
-                                       lh=st[6], nv=st[7], nh=st[8])))
+                                       lh=st[6], nv=st[7], nh=st[8]),
+                            tc=dict(zip(("tc off_p off_red off_gst off_h off_slab slab_rows slab_lbo off_cp cp_bytes "
+                                         "cp_lbo nbuf off_ebuf tmem_cols off_c5 off_dpart").split(), tc))))
         assert len(res) == len(cases)
         return res
     return run
@@ -128,3 +130,46 @@ def test_the_16px_pass_of_the_1mp_workload_takes_longer_box_runs(probe):
     assert p16["lv"] > 8 and p16["lh"] > 8
     for p in (p64, p32):
         assert p["strip"]["TX"] and p["strip"]["lv"] == 8 and p["strip"]["lh"] == 8
+
+
+def test_tensor_core_tiles_keep_every_operand_read_inside_shared_memory(probe):
+    """tcgen05 tiles (16-bit, 50 % overlap with 8/16/32 px steps, r = 4): the
+    MMA operands are read through descriptors, so every address an MMA can form
+    must lie in the tile's shared memory.  A copy buffer's MMAs reach 2048 -
+    (2R + 1) 64 bytes past its last chunk (unused shift slots), the slab's reach
+    (2R above to 16 - 4 below the window) must stay in the slab, and the TMEM
+    columns must cover 16 per window with at most 512 per SM at the occupancy
+    the shared memory allows."""
+    cases = []
+    for s in (8, 16, 32):
+        for prec in (1, 2):
+            for nx, ny in [(1, 1), (2, 3), (7, 5), (31, 31), (127, 127), (63, 9), (159, 89), (11, 255)]:
+                cases.append((2 * s, s, 4, nx, ny, prec))
+    res = probe(cases)
+    R, rows = 4, 4
+    for (w, s, _, nx, ny, prec), r in zip(cases, res):
+        t = r["tc"]
+        assert r["ok"] == 1 and t["tc"] == 1, (w, nx, ny, prec)
+        TX, TY, smem = r["TX"], r["TY"], r["smem"]
+        assert smem <= SMEM_MAX
+        aw, ah = (TX - 1) * s + w, (TY - 1) * s + w
+        nch, ng = aw // 8, (w + 2 * R) // rows
+        assert t["cp_lbo"] == (2 * R + 1) * rows * 16 and t["cp_bytes"] == nch * t["cp_lbo"]
+        assert 2 <= t["nbuf"] <= ng
+        # every address the copies' MMAs can form, for the last buffer, the last window, the last K step
+        reach = t["off_cp"] + (t["nbuf"] - 1) * t["cp_bytes"] + (nch - 1) * t["cp_lbo"] + 2048
+        assert reach <= smem, (w, TX, TY, reach, smem)
+        # the slab: rows 4 g + n of every group, both K chunks of the last window
+        assert rows * (ng - 1) + 16 <= t["slab_rows"]
+        assert t["off_slab"] + nch * t["slab_lbo"] <= t["off_cp"]
+        assert t["off_cp"] + t["nbuf"] * t["cp_bytes"] <= t["off_ebuf"]
+        assert t["off_ebuf"] + 4 * 32 * 20 * 4 <= smem
+        # the buffers over the dead column sums start after the planes, which persist
+        assert t["off_p"] + TX * TY * (2 * R + 1) ** 2 * 4 <= t["off_h"] == t["off_slab"] == t["off_c5"]
+        assert t["off_red"] + 8 * (1 + t["nbuf"]) + 8 <= t["off_gst"]
+        for k in ("off_p", "off_red", "off_slab", "off_cp", "off_ebuf", "cp_bytes", "slab_lbo"):
+            assert t[k] % 16 == 0, k
+        cols = t["tmem_cols"]
+        assert cols >= max(32, 16 * TX) and cols & (cols - 1) == 0 and cols <= 512
+        ctas = min(228 * 1024 // (smem + 1024), 2048 // THREADS)
+        assert ctas * cols <= 512 or 512 // cols >= 2
