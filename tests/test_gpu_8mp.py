@@ -12,6 +12,7 @@ import torch
 import oracle
 import paper_2504_17987_gb300 as rp
 import synth
+from fitcond import well_conditioned
 from synth import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -75,21 +76,25 @@ def test_full_size_pass_matches_oracle_on_sampled_windows(case, w, s, R, precisi
     q = (ky.astype(int) + R) * (2 * R + 1) + (kx.astype(int) + R)
     gap = P.max(axis=2) - np.take_along_axis(P, q[..., None], axis=2)[..., 0]
     disagree = m & ~same
+    vm = m & (valid == 1)
+    wc = vm & well_conditioned(forced.c5)  # the 1e-3 px bound's domain (tests/fitcond.py)
+    assert (vm & ~wc).sum() <= 0.02 * vm.sum()
     if precision == "fp32":
         assert same[m].mean() >= 0.999, f"peak agreement {same[m].mean():.5f}"
         assert (gap[disagree] <= 2e-5).all()
         err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
-        assert err[m & same].max() <= TOL_PX
+        assert err[wc & same].max() <= TOL_PX
         # FP32 rounding alone leaves the median near 2e-7 px; a bias in the
         # deformation weights (e.g. a rounded reciprocal of a step that is not a
         # power of two) shows up as about 2e-6
         assert np.median(err[m & same]) <= 1e-6, f"median {np.median(err[m & same]):.3g} px"
     else:
-        assert same[m].mean() >= 0.99, f"{precision} peak agreement {same[m].mean():.4f}"
+        agree = {"fp16": 0.999, "bf16": 0.99}[precision]
+        assert same[m].mean() >= agree, f"{precision} peak agreement {same[m].mean():.5f}"
         assert (gap[disagree] <= 0.02).all()
     # at the peak the GPU chose, the FP32 refit equals the FP64 refit
     errf = np.maximum(np.abs(u - forced.u), np.abs(v - forced.v))
-    assert errf[m].max() <= TOL_PX, f"refit at the chosen peak: {errf[m].max():.3g}"
+    assert errf[wc].max() <= TOL_PX, f"refit at the chosen peak: {errf[wc].max():.3g}"
 
 
 def test_pipeline_at_8mp_across_precisions(case):

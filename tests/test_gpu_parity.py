@@ -2,11 +2,15 @@
 
 Tolerances (FP32 path): integer peaks identical on >= 99.9 % of windows, every
 disagreement a near-tie of the FP64 plane; u, v within 1e-3 px wherever the
-peaks agree; with the oracle refitted at the GPU's peaks, every window within
-1e-3 px.  BF16/FP16 planes only choose the peak (the stencil is refitted in
-FP32): peaks may differ on near-ties of the bf16-rounded plane, the refit at
-the chosen peak is within 1e-3 px, and the end-to-end field within 0.01 px at
-the 99th percentile.
+peaks agree and the Gaussian fit is well-conditioned (tests/fitcond.py; at
+most 2 % of the windows are not, and their fits must be finite); with the
+oracle refitted at the GPU's peaks, the same.  BF16/FP16 planes only choose
+the peak (the stencil is refitted in FP32): peaks identical on >= 99.9 %
+(FP16) or >= 99 % (BF16) of windows, the others near-ties of the FP64
+plane, the refit at the chosen peak within 1e-3 px, and the end-to-end field
+within 0.01 px at the 99th percentile with at most 0.1 % (1 MP) or 0.2 %
+(512^2) of the vectors beyond 0.01 px.  On the 1 MP workload every stage of
+both forms has >= 99.9 % identical peaks.
 """
 import numpy as np
 import pytest
@@ -15,6 +19,7 @@ import torch
 import oracle
 import paper_2504_17987_gb300 as rp
 import synth
+from fitcond import well_conditioned
 from synth import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -70,18 +75,49 @@ def compare_pass(A, B, w, s, R, pu, pv, precision="fp32", deform="b"):
     return dict(u=u, v=v, valid=valid, ky=ky, kx=kx, ref=ref, forced=forced)
 
 
+# integer peaks identical to the FP64 plane's on at least this share of windows;
+# BF16 keeps 8 significant bits and flips more near-ties than the other forms
+PEAK_AGREE = {"fp32": 0.999, "fp16": 0.999, "bf16": 0.99}
+ILL_MAX = 0.02  # ill-conditioned Gaussian fits (fitcond) allowed among valid windows
+
+
+def check_refit(r, f_u, f_v, c5):
+    """The FP32 refit against an FP64 one at the same peaks: within 1e-3 px
+    where the fit is well-conditioned; finite and rare elsewhere."""
+    valid = r["valid"].astype(bool)
+    wc = well_conditioned(c5) & valid
+    errf = np.maximum(np.abs(r["u"] - f_u), np.abs(r["v"] - f_v))
+    assert errf[wc].max(initial=0.0) <= TOL_PX, f"refit error {errf[wc].max(initial=0.0):.3g}"
+    assert np.isfinite(r["u"]).all() and np.isfinite(r["v"]).all()
+    assert (valid & ~wc).sum() <= ILL_MAX * max(1, valid.sum())
+    return wc
+
+
 def check_fp32_pass(r, R, tie_tol=2e-5):
     ref = r["ref"]
     assert np.array_equal(r["valid"].astype(int), ref.valid)
     same = (r["ky"] == ref.peaks[..., 0]) & (r["kx"] == ref.peaks[..., 1])
-    assert same.mean() >= 0.999, f"peak agreement {same.mean():.5f}"
+    assert same.mean() >= PEAK_AGREE["fp32"], f"peak agreement {same.mean():.5f}"
     assert near_tie_ok(ref.plane, r["ky"], r["kx"], R, tie_tol)[~same].all()
+    wc = check_refit(r, r["forced"].u, r["forced"].v, r["forced"].c5)
     err = np.maximum(np.abs(r["u"] - ref.u), np.abs(r["v"] - ref.v))
-    assert err[same].max() <= TOL_PX, f"max |du,dv| at agreeing peaks {err[same].max():.3g}"
-    f = r["forced"]
-    errf = np.maximum(np.abs(r["u"] - f.u), np.abs(r["v"] - f.v))
-    assert errf.max() <= TOL_PX, f"max refit error {errf.max():.3g}"
-    return same.mean(), err.max()
+    ok = same & wc
+    assert err[ok].max(initial=0.0) <= TOL_PX, f"max |du,dv| at agreeing peaks {err[ok].max(initial=0.0):.3g}"
+    return same.mean(), err[ok].max(initial=0.0)
+
+
+def check_16bit_pass(r, R, precision, tie_tol=0.02):
+    """BF16/FP16 planes choose the peak: identical to the FP64 plane's on at
+    least PEAK_AGREE of the windows, every disagreement a near-tie of the FP64
+    plane (within tie_tol of its maximum), and the FP32 refit at the chosen
+    peak within 1e-3 px of the FP64 refit at that peak (well-conditioned fits)."""
+    ref = r["ref"]
+    assert np.array_equal(r["valid"].astype(int), ref.valid)
+    same = (r["ky"] == ref.peaks[..., 0]) & (r["kx"] == ref.peaks[..., 1])
+    assert same.mean() >= PEAK_AGREE[precision], f"{precision} peak agreement {same.mean():.5f}"
+    assert near_tie_ok(ref.plane, r["ky"], r["kx"], R, tie_tol)[~same].all()
+    check_refit(r, r["forced"].u, r["forced"].v, r["forced"].c5)
+    return same.mean()
 
 
 # ----------------------------------------------------------------- stages ---
@@ -126,22 +162,22 @@ def test_correlate_with_predictor_fp32(w, s, R, form, monkeypatch):
     check_fp32_pass(r, R)
 
 
+@pytest.mark.parametrize("kernel", ["tcgen05", "mma"])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 @pytest.mark.parametrize("w,s,R", [(64, 32, 4), (32, 16, 4), (16, 8, 4), (32, 8, 8), (48, 24, 6), (24, 12, 6)])
-def test_correlate_tensor_core_planes(precision, w, s, R):
+def test_correlate_tensor_core_planes(precision, w, s, R, kernel, monkeypatch):
+    # 50 % overlap with 8/16/32 px steps at r = 4 runs the tcgen05 kernel; the
+    # mma.sync kernel covers the other shapes, and these when RPIV_TC_PLANES=0
+    if kernel == "mma":
+        monkeypatch.setenv("RPIV_TC_PLANES", "0")
+    elif not (R == 4 and w == 2 * s):
+        pytest.skip("shape runs the mma.sync kernel only")
     wk = wl.paper_1mp(W=320, H=288)
     A, B = wk.render()
     nx, ny = oracle.grid_n(320, w, s), oracle.grid_n(288, w, s)
     pu, pv = smooth_field(nx, ny, w, s, seed=w * 17 + R, base=(12.0, 0.0))
     r = compare_pass(A, B, w, s, R, pu, pv, precision=precision)
-    ref = r["ref"]
-    same = (r["ky"] == ref.peaks[..., 0]) & (r["kx"] == ref.peaks[..., 1])
-    # the 16-bit plane chooses the peak; disagreements must be near-ties of the FP64 plane
-    assert same.mean() >= 0.99, f"{precision} peak agreement {same.mean():.4f}"
-    assert near_tie_ok(ref.plane, r["ky"], r["kx"], R, 0.02)[~same].all()
-    f = r["forced"]
-    errf = np.maximum(np.abs(r["u"] - f.u), np.abs(r["v"] - f.v))
-    assert errf.max() <= TOL_PX, f"refit at the chosen peak: {errf.max():.3g}"
+    check_16bit_pass(r, R, precision)
 
 
 def test_correlate_central_deformation():
@@ -230,18 +266,116 @@ def test_pipeline_plain_256_end_to_end():
     assert np.abs(om - ref.vort).max() <= 2e-4
 
 
-def test_pipeline_paper_1mp_end_to_end_stagewise():
-    """1 MP, 12-bit, pyramid + 64 -> 32 -> 16: end-to-end statistics, and each
-    pass against the oracle fed the GPU's own predictor for that pass."""
+def gpu_schedule_by_stages(A, B, sched, precision):
+    """The engine's schedule composed from the stage entry points on the GPU:
+    2x2 pyramid levels; at the coarsest a pass with a zero predictor, at each
+    finer level a pass predicted by the level above (interpolated one level
+    up); then the full-resolution passes, each predicted by the previous;
+    outlier detection after every pass; vorticity of the last field.  Returns
+    the per-stage records (the GPU's own predictor, raw result and validated
+    field) and the final (u, v, vorticity, mask)."""
+    H, W = A.shape
+    steps = [oracle.step_of(w, o) for w, o in zip(sched.windows, sched.overlaps)]
+    L = sched.levels
+    a, b = dev(A), dev(B)
+    levels = [(a, b, A.astype(np.float64), B.astype(np.float64))]
+    for _ in range(L):
+        ad, bd = rp.stage_downsample(levels[-1][0]), rp.stage_downsample(levels[-1][1])
+        levels.append((ad, bd, ad.cpu().numpy().astype(np.float64), bd.cpu().numpy().astype(np.float64)))
+    w0, s0, r0 = sched.windows[0], steps[0], sched.radii[0]
+    stages, field = [], None
+
+    def run(kind, idx, al, bl, Al, Bl, w, s, r, pu, pv):
+        u, v, info = rp.stage_correlate(al, bl, w, s, r, pu, pv, precision=precision)
+        uu, vv, mk = rp.stage_validate(u, v, info, sched.uod_threshold, sched.uod_eps, sched.replace)
+        torch.cuda.synchronize()
+        ny, nx = u.shape
+        npf = (lambda t: np.zeros((ny, nx)) if t is None else t.cpu().numpy().astype(np.float64))
+        stages.append(dict(kind=kind, idx=idx, A=Al, B=Bl, w=w, s=s, r=r, pu=npf(pu), pv=npf(pv),
+                           u=u.cpu().numpy(), v=v.cpu().numpy(), info=info.cpu().numpy(),
+                           uu=uu.cpu().numpy(), vv=vv.cpu().numpy(), mk=mk.cpu().numpy()))
+        return uu, vv, mk
+
+    for lvl in range(L, 0, -1):
+        al, bl, Al, Bl = levels[lvl]
+        nxl, nyl = oracle.grid_n(Al.shape[1], w0, s0), oracle.grid_n(Al.shape[0], w0, s0)
+        pu = pv = None
+        if field is not None:
+            pu, pv = rp.stage_interp(field[0], field[1], w0, s0, nxl, nyl, w0, s0, 1)
+        uu, vv, _ = run("level", lvl, al, bl, Al, Bl, w0, s0, r0, pu, pv)
+        field = (uu, vv)
+    nx0, ny0 = oracle.grid_n(W, w0, s0), oracle.grid_n(H, w0, s0)
+    pu = pv = None
+    if field is not None:
+        pu, pv = rp.stage_interp(field[0], field[1], w0, s0, nx0, ny0, w0, s0, 1)
+    for p, (w, s, r) in enumerate(zip(sched.windows, steps, sched.radii)):
+        if p > 0:
+            pw, ps = sched.windows[p - 1], steps[p - 1]
+            pu, pv = rp.stage_interp(uu, vv, pw, ps, oracle.grid_n(W, w, s), oracle.grid_n(H, w, s), w, s, 0)
+        uu, vv, mk = run("pass", p, a, b, levels[0][2], levels[0][3], w, s, r, pu, pv)
+    om = rp.stage_vorticity(uu, vv, steps[-1])
+    return stages, tuple(t.cpu().numpy() for t in (uu, vv, om, mk))
+
+
+def check_stage(st, precision):
+    """One stage against the oracle fed the GPU's own predictor for it: the
+    pass (peaks, u, v, refit at the GPU's peaks) and the outlier test on the
+    GPU's raw field."""
+    R = st["r"]
+    ref = oracle.correlate_pass(st["A"], st["B"], st["w"], st["s"], R, st["pu"].astype(np.float32).astype(np.float64),
+                                st["pv"].astype(np.float32).astype(np.float64), want_plane=True)
+    info = torch.from_numpy(st["info"])
+    valid, ky, kx = [t.numpy() for t in rp.decode_info(info)]
+    forced = oracle.correlate_pass(st["A"], st["B"], st["w"], st["s"], R,
+                                   st["pu"].astype(np.float32).astype(np.float64),
+                                   st["pv"].astype(np.float32).astype(np.float64),
+                                   force_peaks=np.stack([ky, kx], -1).astype(np.int32))
+    r = dict(u=st["u"], v=st["v"], valid=valid, ky=ky, kx=kx, ref=ref, forced=forced)
+    if precision == "fp32":
+        agree, _ = check_fp32_pass(r, R)
+    else:
+        agree = check_16bit_pass(r, R, precision)
+    # the 1 MP workload: >= 99.9 % identical peaks at every stage, every form
+    assert agree >= 0.999, f"{precision} {st['kind']} {st['idx']}: peak agreement {agree:.5f}"
+    ru, rv, rm = oracle.uod(st["u"].astype(np.float64), st["v"].astype(np.float64), st["info"] & 1, 2.0, 0.1, True)
+    assert np.array_equal(st["mk"], rm)
+    assert np.abs(st["uu"] - ru).max() <= 1e-6 and np.abs(st["vv"] - rv).max() <= 1e-6
+    return agree
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_pipeline_paper_1mp_stagewise(precision):
+    """The 1 MP workload (12-bit, pyramid + 64 -> 32 -> 16, +-4): every pyramid
+    level and every pass against the oracle fed the GPU's own predictor for
+    that stage, at the bound of each form (integer peaks identical on
+    >= 99.9 % of windows, disagreements near-ties of the FP64 plane; FP32: u, v
+    within 1e-3 px at agreeing peaks; every form: the FP32 refit at the GPU's
+    peaks within 1e-3 px); the stage composition equals the engine's result;
+    end to end against the oracle."""
     w = wl.paper_1mp()
     A, B = w.render()
     sc = w.schedule
-    u, v, om, m = run_engine(A, B, sc, 12)
+    stages, (u, v, om, m) = gpu_schedule_by_stages(A, B, sc, precision)
+    assert [(st["kind"], st["idx"]) for st in stages] == [("level", 2), ("level", 1), ("pass", 0), ("pass", 1),
+                                                           ("pass", 2)]
+    for st in stages:
+        check_stage(st, precision)
+    # the engine computes the same schedule
+    eu, ev, eom, em = run_engine(A, B, sc, 12, precision=precision)
+    assert np.mean(np.maximum(np.abs(eu - u), np.abs(ev - v)) <= 1e-5) >= 0.999
+    assert np.mean(em == m) >= 0.999
+    # end to end
     ref = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels)
-    err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
-    assert np.mean(err <= TOL_PX) >= 0.99, f"within 1e-3: {np.mean(err <= TOL_PX):.4f}"
-    assert np.percentile(err, 99) <= 0.05
-    assert np.mean(m == ref.mask) >= 0.99
+    err = np.maximum(np.abs(eu - ref.u), np.abs(ev - ref.v))
+    if precision == "fp32":
+        assert np.mean(err <= TOL_PX) >= 0.999, f"within 1e-3: {np.mean(err <= TOL_PX):.5f}"
+        assert np.percentile(err, 99) <= 1e-4, f"p99 {np.percentile(err, 99):.3g}"
+    else:
+        # the stated bound of the 16-bit forms: p99 <= 0.01 px, and at most 0.1 % of
+        # the vectors (near-tie peak flips) beyond 0.01 px
+        assert np.percentile(err, 99) <= 0.01, f"p99 {np.percentile(err, 99):.4f}"
+        assert np.mean(err > 0.01) <= 1e-3, f"beyond 0.01 px: {np.mean(err > 0.01):.5f}"
+    assert np.mean(em == ref.mask) >= 0.999
 
 
 @pytest.mark.parametrize("form", ["tiles", "strips"])
@@ -302,14 +436,16 @@ def test_split_batch_equals_pairs_alone():
     eng.close()
 
 
-def test_pipeline_bf16_within_0p01_px():
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_pipeline_16bit_within_0p01_px(precision):
     w = wl.paper_1mp(W=512, H=512)
     A, B = w.render()
     sc = w.schedule
-    u, v, _, _ = run_engine(A, B, sc, 12, precision="bf16")
+    u, v, _, _ = run_engine(A, B, sc, 12, precision=precision)
     ref = oracle.process_pair(A, B, sc.windows, sc.overlaps, sc.radii, sc.levels)
     err = np.maximum(np.abs(u - ref.u), np.abs(v - ref.v))
     assert np.percentile(err, 99) <= 0.01, f"p99 {np.percentile(err, 99):.4f}"
+    assert np.mean(err > 0.01) <= 2e-3, f"beyond 0.01 px: {np.mean(err > 0.01):.5f}"
 
 
 def test_pipeline_paper_exact_variant_central_warp_zero_radius():
@@ -360,12 +496,7 @@ def test_correlate_edge_shapes(w, s, R, precision):
     if precision == "fp32":
         check_fp32_pass(r, R)
     else:
-        ref = r["ref"]
-        same = (r["ky"] == ref.peaks[..., 0]) & (r["kx"] == ref.peaks[..., 1])
-        assert same.mean() >= 0.98, f"{precision} peak agreement {same.mean():.4f}"
-        assert near_tie_ok(ref.plane, r["ky"], r["kx"], R, 0.02)[~same].all()
-        f = r["forced"]
-        assert np.maximum(np.abs(r["u"] - f.u), np.abs(r["v"] - f.v)).max() <= TOL_PX
+        check_16bit_pass(r, R, precision)
 
 
 def test_tensor_core_path_rejects_windows_beyond_shared_memory():
