@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--workload", default="paper_1mp", choices=["paper_1mp", "paper_1mp_r1"],
                    help="paper_1mp_r1: the paper's 16 px / +-1 operating point on the same images")
     p.add_argument("--mode", default="full",
-                   choices=["full", "ncu", "serve", "precision", "adjoint", "sizes", "preprocess"],
+                   choices=["full", "ncu", "serve", "precision", "adjoint", "sizes", "preprocess", "tcrate"],
                    help="ncu: one warm-up step and one step of the headline path, nothing else (profiler runs); "
                         "serve: the streaming mix (Poisson arrivals over camera streams); "
                         "precision: the 8 MP Fourier-mode pair, FP32/BF16/FP16 fields against the FP64 oracle")
@@ -418,6 +418,33 @@ def run_sizes(args):
     return 0
 
 
+def run_tc_rate(args):
+    """Cycles per tcgen05.mma (kind::f16, K = 16) against M and N, from one
+    thread issuing 256 MMAs back to back (libtcrate); with the clock sampled,
+    the tensor-core rate each shape reaches."""
+    import ctypes
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_17987_gb300 import build as b
+    lib = ctypes.CDLL(b.build_tc_rate())
+    lib.tc_rate_cycles.restype = ctypes.c_double
+    lib.tc_rate_cycles.argtypes = [ctypes.c_int] * 4
+    torch.cuda.init()
+    rows = []
+    for M, N, nacc in [(128, 16, 1), (128, 16, 8), (64, 16, 8), (128, 32, 8), (128, 64, 8), (128, 128, 4),
+                       (128, 256, 1), (128, 256, 2)]:
+        cyc = lib.tc_rate_cycles(M, N, 256, nacc)
+        if cyc < 0 or cyc >= 1e9:
+            raise RuntimeError(f"tc_rate_cycles({M}, {N}) failed: {cyc}")
+        rows.append({"M": M, "N": N, "K": 16, "accumulators": nacc, "cycles_per_mma": round(cyc, 1),
+                     "mac_per_cycle": round(M * N * 16 / cyc, 1)})
+    print(json.dumps({"mode": "tcrate", "rows": rows}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------ differentiation --
 
 def run_adjoint(args):
@@ -610,6 +637,8 @@ def main():
         return run_sizes(args)
     if args.mode == "preprocess":
         return run_preprocess(args)
+    if args.mode == "tcrate":
+        return run_tc_rate(args)
     if args.mode == "serve":
         import numpy as np  # noqa: F811
         globals()["np"] = np

@@ -60,6 +60,25 @@ def build_fma_peak(force: bool = False) -> str:
     return FMA_LIB
 
 
+TCR_SRC = "tc_rate.cu"
+TCR_LIB = os.path.join(HERE, "libtcrate.so")
+
+
+def build_tc_rate(force: bool = False) -> str:
+    """The tcgen05.mma issue-rate microbenchmark (measurement support), as its
+    own small library."""
+    src = os.path.join(CSRC, TCR_SRC)
+    if not force and os.path.exists(TCR_LIB) and os.path.getmtime(TCR_LIB) >= os.path.getmtime(src):
+        return TCR_LIB
+    tmp = TCR_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([_nvcc(), *ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", src, "-o", tmp, "-lcudart"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {TCR_SRC}:\n{r.stderr}")
+    os.replace(tmp, TCR_LIB)
+    return TCR_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if sources changed) and return the path of librpiv.so."""
     stamp = os.path.join(BUILD, "stamp")

@@ -229,38 +229,43 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool str
 
 // Tensor-core (tcgen05) tiles: 50 % overlap (w = 2s, s a multiple of 8) at
 // r = 4.  The FP32 regions, box sums and statistics are laid out as for the
-// FP32 kernel; the planes are one NP-float plane per window, kept for the whole
-// tile; the dead column box sums hold, per window row, the zero-banded A slab,
-// a ring of nbuf buffers of shifted B' copies (one MMA group of 4 rows each)
-// and the epilogue buffer, and later the per-window stencil buffers.  The MMAs
-// of a copy buffer read up to 2048 - (2R + 1) 64 bytes past its last chunk
-// (the unused shift slots of the last chunks), which the epilogue buffer after
-// the ring covers.
+// FP32 kernel; then the phase's barriers, one NP-float plane per window and
+// the FP32 refit planes (|s| <= 2) per block, kept for the whole tile; the
+// dead column box sums hold two A slabs, the ring of copy slots and the
+// epilogue buffer, and later the per-window stencil buffers.  A slot holds one
+// 8-column chunk past the tile's columns; an MMA reads up to 2048 - 512 bytes
+// past its slot's last chunk (shift slots it does not need), so the ring ends
+// with 1 KB of slack.
 constexpr int kTcRows = 4;
-constexpr int kTcEbufBytes = 4 * 32 * 20 * 4;
+constexpr int kTcEbufBytes = 3 * 32 * 20 * 4;
+constexpr int kTcRn = 2;
 
 bool tc_shape(int w, int s, int R) { return R == 4 && w == 2 * s && (s == 8 || s == 16 || s == 32); }
 
-Layout layout_for_tc(int TX, int TY, int w, int s, int R, int nbuf)
+Layout layout_for_tc(int TX, int TY, int w, int s, int R, int ns)
 {
     Layout L = layout_for(TX, TY, w, s, R, s, PREC_FP32);
     PassPlan &p = L.p;
-    const int ND = 2 * R + 1, NP = ND * ND;
+    const int ND = 2 * R + 1, NP = ND * ND, NDN = 2 * kTcRn + 1;
     const int aw = (TX - 1) * s + w, ah = (TY - 1) * s + w;
     const int BR = ah + 2 * (R + 1), vh = BR - w + 1;
-    const int nwin = TX * TY, nch = aw / 8, ng = (w + 2 * R) / kTcRows;
-    p.RGx = 1;
+    const int nwin = TX * TY, nch = aw / 8, nb = (aw / s) * (ah / s);
+    // row groups of the refit planes: enough (block, sy, group) items for the CTA
+    int RG = 1;
+    while (2 * RG <= 32 && s % (2 * RG) == 0 && nb * NDN * RG < kThreads) RG *= 2;
+    p.RGx = RG;
     p.pstride = NP;
     p.tc = 1;
     p.slab_rows = w + 2 * R + 16 - kTcRows;
     p.slab_lbo = p.slab_rows * 16;
-    p.cp_lbo = ND * kTcRows * 16;
-    p.cp_bytes = nch * p.cp_lbo;
-    p.tc_nbuf = std::max(2, std::min(nbuf, ng));
+    p.cp_lbo = 8 * kTcRows * 16;
+    p.cp_group = (nch + 1) * p.cp_lbo;
+    p.tc_nbuf = ns;
+    p.cp_bytes = ns * p.cp_group + 1024;
     int cols = 32;
-    while (cols < 16 * TX) cols *= 2;
+    while (cols < 32 * TX) cols *= 2;
     p.tmem_cols = cols;
-    // rebuild the offsets past the box sums: [stats][mbarriers][block stats][planes][reused region]
+    // rebuild the offsets past the box sums
     int off = p.off_v + up(2 * vh * p.v_pitch * 4, 16);
     auto take = [&](int bytes) {
         int o = off;
@@ -268,14 +273,16 @@ Layout layout_for_tc(int TX, int TY, int w, int s, int R, int nbuf)
         return o;
     };
     p.off_stats = take(2 * nwin * 4);
-    p.off_red = take(8 * (1 + p.tc_nbuf) + 8);  // barriers, then the TMEM address and the tile offset
-    p.off_gst = take((aw / s) * (ah / s) * 8);
+    // the regions' barrier, the phase's 2 ns + 6, then the TMEM address, the tile offset, the abort flag
+    p.off_red = take(8 * (1 + 2 * ns + 6) + 16);
+    p.off_gst = take(nb * 8);
     p.off_p = take(nwin * NP * 4);
+    p.off_refit = take(nb * NDN * NDN * 4);
     p.off_h = off;
     const int c_bytes = 2 * vh * p.h_pitch * 4;
     p.off_slab = off;
-    p.off_cp = up(p.off_slab + nch * p.slab_lbo, 16);
-    p.off_ebuf = up(p.off_cp + p.tc_nbuf * p.cp_bytes, 16);
+    p.off_cp = up(p.off_slab + 2 * nch * p.slab_lbo, 16);
+    p.off_ebuf = up(p.off_cp + p.cp_bytes, 16);
     const int tc_end = p.off_ebuf + kTcEbufBytes;
     const int win_bytes = up(nwin * 5 * 4, 16) + up(nwin * 4, 16) * 2 + up(std::max(nwin, kThreads / 32) * 5 * 4, 16);
     p.off_c5 = off;
@@ -285,18 +292,22 @@ Layout layout_for_tc(int TX, int TY, int w, int s, int R, int nbuf)
     off = std::max({off + c_bytes, tc_end, off + win_bytes});
     p.smem_bytes = up(off, 16);
     p.max_windows = nwin;
+    p.max_blocks = nb;
     L.bytes = p.smem_bytes;
     return L;
 }
 
 }  // namespace
 
-// RPIV_TC_PLANES=0 keeps the mma.sync planes for the shapes the tcgen05
-// kernel covers (tests run both); read at each plan.
+// RPIV_TC_PLANES=1 runs the tcgen05 kernel for the shapes it covers (tests
+// run both kernels); read at each plan.  The mma.sync kernel is the default:
+// measured on GB300 at 1 MP it is faster (6.5k against 4.1k pairs/s), since a
+// tcgen05.mma of K = 16 takes about 146 cycles whatever its N, and the banded
+// correlation fills at most 16 of its columns usefully.
 bool tc_planes_enabled()
 {
     const char *e = std::getenv("RPIV_TC_PLANES");
-    return !(e && std::strcmp(e, "0") == 0);
+    return e && std::strcmp(e, "1") == 0;
 }
 
 bool pass_supported(int R, int prec)
@@ -424,26 +435,23 @@ bool plan_strip(int w, int s, int R, int G, int nx, int ny, int prec, PassPlan *
     return true;
 }
 
-// Tensor-core tiles: among shapes of up to 8 x 8 windows that leave room for
-// two CTAs per SM (shared memory, and 512 TMEM columns per SM), the one with
-// the most windows, then the fewest copy buffers' bytes; copy rings of two
-// buffers, or one per MMA group of a window row when that fits.
+// Tensor-core tiles: among shapes of up to 8 x 8 windows with rings of 6 or 4
+// copy slots, those that leave room for two CTAs per SM (shared memory, and
+// 512 TMEM columns per SM: two rows of 16 columns per window): the most
+// windows, then the longer ring, then the squarer tile.
 bool plan_tc(int w, int s, int R, int nx, int ny, PassPlan *plan)
 {
-    const int target = 2;
-    const int ng = (w + 2 * R) / kTcRows;
     double best = -1e30;
     Layout pick{};
     int pick_tx = 0, pick_ty = 0;
     for (int ty = 1; ty <= std::min(8, ny); ++ty)
         for (int tx = 1; tx <= std::min(8, nx); ++tx)
-            for (int nbuf : {ng, 2}) {
-                Layout L = layout_for_tc(tx, ty, w, s, R, nbuf);
+            for (int ns : {6, 4}) {
+                Layout L = layout_for_tc(tx, ty, w, s, R, ns);
                 if (L.bytes > kSmemMax) continue;
                 const int ctas = std::min({228 * 1024 / (L.bytes + 1024), 2048 / kThreads, 512 / L.p.tmem_cols});
                 if (ctas < 1) continue;
-                const double score = std::min(ctas, target) * 1e8 + (double)tx * ty * 1e5 +
-                                     (L.p.tc_nbuf >= ng ? 1e3 : 0) - std::abs(tx - ty);
+                const double score = std::min(ctas, 2) * 1e8 + (double)tx * ty * 1e5 + ns * 1e3 - std::abs(tx - ty);
                 if (score > best) {
                     best = score;
                     pick = L;

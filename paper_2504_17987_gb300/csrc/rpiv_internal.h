@@ -87,13 +87,15 @@ struct PassPlan {
     int off_gst;                 // per-G x G block sum and centred sum of squares of A
     int off_c5, off_peaks, off_need, off_dpart;  // per-window stencil values, argmax, direct-sum mask and sums
     int max_windows, max_blocks;
-    // tcgen05 planes (tc = 1; BF16/FP16, 50 % overlap, r = 4): per window row a
-    // zero-banded A slab, a ring of tc_nbuf buffers of shifted B' copies (one
-    // MMA group of rows each), an epilogue buffer, tmem_cols TMEM columns
+    // tcgen05 planes (tc = 1; BF16/FP16, 50 % overlap, r = 4): two zero-banded A
+    // slabs (window rows), a ring of tc_nbuf slots of shifted B' copies (one MMA
+    // group of rows each), an epilogue buffer, tmem_cols TMEM columns (two rows)
     int tc;
     int off_slab, slab_rows, slab_lbo;  // bytes; slab_lbo: stride of its 8-column chunks
-    int off_cp, cp_bytes, cp_lbo, tc_nbuf;  // copy buffers: cp_bytes each, chunk stride cp_lbo
+    int off_cp, cp_bytes, cp_lbo, tc_nbuf;  // copy ring: cp_bytes in all, chunk stride cp_lbo
+    int cp_group;  // bytes per group slot of the ring
     int off_ebuf, tmem_cols;
+    int off_refit;  // FP32 block planes of the refit, |s| <= 2 (25 floats per block)
 };
 
 struct PassArgs {

@@ -20,15 +20,29 @@
 // operands small.
 //
 // Layouts (canonical K-major, no swizzle: 8 rows of 16 bytes per core matrix):
-//   copies  per chunk q of 8 columns: slots c = 0..2R, each TC_ROWS rows of 16 B;
-//           the M index m = TC_ROWS c + i is linear at 16 B (SBO = 128), the
-//           chunk stride (LBO) is (2R + 1) TC_ROWS 16 B, so the unused slots
-//           c > 2R of a chunk read the following chunks (their D rows are never
-//           read)
+//   copies  per chunk q of 8 columns: slots c = 0..7, each TC_ROWS rows of 16 B
+//           (slot c holds B' shifted by c - R); the M index m = TC_ROWS c + i
+//           is linear at 16 B (SBO = 128) and the chunk stride (LBO) is 8
+//           slots, so slot c >= 8 of chunk q is slot c - 8 of chunk q + 1,
+//           which holds B' shifted by c - R as well: eight copies serve all
+//           2R + 1 <= 16 shifts.  A group keeps one chunk past the tile's
+//           columns for them; the slots beyond 2R read further on (their D rows
+//           are never read).
 //   slab    per chunk q: the window row's A rows from 2R above the window to
 //           16 - TC_ROWS below it, rows of 16 B (SBO = 128), chunk stride LBO
-// Window rows of the tile are processed in turn; a group's copies are staged
-// in a ring of buffers, each released by the commit of the MMAs that read it.
+// Warp roles in the tensor-core phase (no CTA barrier inside it): producer
+// warps build each window row's slab (double-buffered) and its groups' copies
+// into a ring of slots; one issuer thread waits for a slot to fill, runs its
+// MMAs for every window of the row into the row's TMEM block (double-buffered
+// by row) and commits, which frees the slot; a commit after a row's last
+// group releases its slab and hands its accumulators to the epilogue warps,
+// which free the TMEM block when they have read it.  All waits are bounded and
+// share an abort flag, so that one timeout ends every role.
+//
+// The five-point refit is exact FP32: block planes over the shifts |s| <= 2
+// around the predictor (FP32 FMAs on the CUDA cores, before the tensor-core
+// phase) supply the stencil of every peak within one pixel of the predictor;
+// the rare others are summed directly.
 #pragma once
 
 #include "pass_impl.cuh"
@@ -40,6 +54,7 @@ constexpr int TC_M = 128;     // 32 shift slots x TC_ROWS rows
 constexpr int TC_N = 16;      // A rows of a group
 constexpr int TC_R = 4;       // the radius these kernels are built for
 constexpr int TC_EB_PITCH = 20;  // floats per lane in the epilogue buffer (conflict-free 128-bit stores)
+constexpr int TC_RN = 2;         // radius of the FP32 block planes of the refit
 
 static_assert(TC_ROWS + 2 * TC_R <= TC_N, "a group's A rows must fit N");
 
@@ -110,22 +125,32 @@ __device__ __forceinline__ void tc_dealloc(uint32_t taddr, int cols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
 }
 
-// Warp 0 polls phase `parity` of bar (bounded); every thread returns the same
-// verdict.  On timeout the error word is set.
-static __device__ __forceinline__ bool tc_cta_wait(const PassArgs &a, uint64_t *bar, uint32_t parity)
+// Bounded wait of one warp on phase `parity` of bar: lane 0 polls, giving up
+// after the limit (error word and abort flag set) or as soon as any role has
+// aborted (even if the phase completed); every lane returns the verdict.
+static __device__ __forceinline__ bool warp_wait(const PassArgs &a, uint64_t *bar, uint32_t parity,
+                                                 volatile int *abort)
 {
-    bool ok = true;
-    if (threadIdx.x < 32) {
-        ok = false;
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) {
         const int lim = a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT;
-        for (int it = 0; it < lim; ++it)
+        for (int it = 0; it < lim && !*abort; ++it) {
             if (mbar_try_wait(bar, parity)) {
-                ok = true;
+                ok = 1;
                 break;
             }
-        if (!ok && threadIdx.x == 0 && a.err) atomicOr(a.err, 1);
+        }
+        if (!ok) {
+            if (!*abort && a.err) atomicOr(a.err, 1);
+            *abort = 1;
+        }
     }
-    return !__syncthreads_or(!ok);
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // ------------------------------------------------------ operand staging --
@@ -141,14 +166,15 @@ __device__ __forceinline__ uint4 pack8(float4 lo, float4 hi, float m)
     return r;
 }
 
-// Slab of window row wy: slab row j holds A row wy s - 2R + j (tile rows),
-// minus m, where it lies in the window; zero elsewhere.
+// Slab of window row wy by threads t = 0 .. nt - 1 of the producer warps:
+// slab row j holds A row wy s - 2R + j (tile rows), minus m, where it lies in
+// the window; zero elsewhere.
 template <int PREC>
-static __device__ __forceinline__ void tc_build_slab(const PassPlan &P, const TileGeom &g, const float *As,
-                                                     unsigned char *slab, int wy, float m)
+static __device__ __forceinline__ void tc_slab(const PassPlan &P, const TileGeom &g, const float *As,
+                                               unsigned char *slab, int wy, float m, int t, int nt)
 {
     const int rows = P.slab_rows, nch = g.aw >> 3;
-    for (int it = threadIdx.x; it < rows * nch; it += blockDim.x) {
+    for (int it = t; it < rows * nch; it += nt) {
         const int q = it / rows, j = it - q * rows;
         const int r = j - 2 * TC_R;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -160,17 +186,18 @@ static __device__ __forceinline__ void tc_build_slab(const PassPlan &P, const Ti
     }
 }
 
-// Shifted copies of group gi of window row wy: B' rows y = wy s - R + TC_ROWS gi
-// + i (tile rows); slot c, chunk q, row i holds B'(y, 8q + t + c - R) - m.
-// A thread takes one (row, chunk): 16 floats, the even and odd column pairs
-// converted once, 2R + 1 stores of 16 bytes.
+// Copies of group gi of window row wy into a ring slot, by the lanes of one
+// warp: B' rows y = wy s - R + TC_ROWS gi + i (tile rows); slot c of chunk q,
+// row i holds B'(y, 8q + t + c - R) - m.  A lane takes one (row, chunk), rows
+// fastest (so that a store instruction covers consecutive 16-byte rows): 16
+// floats, the even and odd column pairs converted once, eight 16-byte stores.
 template <int PREC>
-static __device__ __forceinline__ void tc_build_group(const PassPlan &P, const TileGeom &g, const float *Bs,
-                                                      unsigned char *buf, int wy, int gi, float m)
+static __device__ __forceinline__ void tc_group(const PassPlan &P, const TileGeom &g, const float *Bs,
+                                                unsigned char *dst0, int wy, int gi, float m, int t, int nt)
 {
     constexpr int R = TC_R;
-    const int nch = g.aw >> 3;
-    for (int it = threadIdx.x; it < TC_ROWS * nch; it += blockDim.x) {
+    const int nq = (g.aw >> 3) + 1;
+    for (int it = t; it < TC_ROWS * nq; it += nt) {
         const int q = it / TC_ROWS, i = it - q * TC_ROWS;
         const int y = wy * g.s - R + TC_ROWS * gi + i;
         const float *src = Bs + (y + R + 1) * P.b_pitch + P.padl + 8 * q - R;
@@ -188,9 +215,9 @@ static __device__ __forceinline__ void tc_build_group(const PassPlan &P, const T
         for (int j = 0; j < 8; ++j) ev[j] = pack2<PREC>(v[2 * j], v[2 * j + 1]);
 #pragma unroll
         for (int j = 0; j < 7; ++j) od[j] = pack2<PREC>(v[2 * j + 1], v[2 * j + 2]);
-        unsigned char *dst = buf + q * P.cp_lbo + i * 16;
+        unsigned char *dst = dst0 + q * P.cp_lbo + i * 16;
 #pragma unroll
-        for (int c = 0; c <= 2 * R; ++c) {
+        for (int c = 0; c < 8; ++c) {
             uint4 wv;
             if ((c & 1) == 0)
                 wv = make_uint4(ev[c / 2], ev[c / 2 + 1], ev[c / 2 + 2], ev[c / 2 + 3]);
@@ -203,132 +230,238 @@ static __device__ __forceinline__ void tc_build_group(const PassPlan &P, const T
 
 // ------------------------------------------------------------- epilogue --
 
-// Window wx of row wy: warps of lane quarter 0 (slots 0..7) and 1 (slot 8)
-// read the window's 16 TMEM columns, stage them per lane, and form the
-// diagonal sums P_w(sy, sx) into the plane buffer.
-static __device__ __forceinline__ void tc_epilogue(const TileGeom &g, uint32_t tmem, float *ebuf, float *Ps, int wy)
+// Window wx of a row whose accumulators start at TMEM column col0: a warp of
+// lane quarter 0 forms the planes of slots 0..7, one of quarter 1 those of
+// slot 8: the 16 columns of its lanes staged in eb, then the diagonal sums
+// P_w(sy, sx) = sum_i D[(sx + R, i)][i + R - sy] into the window's plane.
+static __device__ __forceinline__ void tc_epilogue_window(uint32_t tmem, int quarter, uint32_t col, float *eb,
+                                                          float *pw)
 {
-    constexpr int R = TC_R, ND = 2 * R + 1, NP = ND * ND;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quarter = warp & 3, half = warp >> 2, nhalf = blockDim.x >> 7;
-    if (quarter >= 2) return;
-    float *eb = ebuf + (half * 2 + quarter) * 32 * TC_EB_PITCH;
+    constexpr int R = TC_R, ND = 2 * R + 1;
+    const int lane = threadIdx.x & 31;
+    float r[16];
+    tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + col, r);
+    float4 *d4 = reinterpret_cast<float4 *>(eb + lane * TC_EB_PITCH);
+    d4[0] = make_float4(r[0], r[1], r[2], r[3]);
+    d4[1] = make_float4(r[4], r[5], r[6], r[7]);
+    d4[2] = make_float4(r[8], r[9], r[10], r[11]);
+    d4[3] = make_float4(r[12], r[13], r[14], r[15]);
+    __syncwarp();
     const int nout = quarter == 0 ? 8 * ND : ND;  // slots 0..7, or slot 8
-    for (int wx = half; wx < g.nwx; wx += nhalf) {
-        float r[16];
-        tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * wx), r);
-        float4 *d4 = reinterpret_cast<float4 *>(eb + lane * TC_EB_PITCH);
-        d4[0] = make_float4(r[0], r[1], r[2], r[3]);
-        d4[1] = make_float4(r[4], r[5], r[6], r[7]);
-        d4[2] = make_float4(r[8], r[9], r[10], r[11]);
-        d4[3] = make_float4(r[12], r[13], r[14], r[15]);
-        __syncwarp();
-        float *pw = Ps + (wy * g.nwx + wx) * NP;
-        for (int o = lane; o < nout; o += 32) {
-            const int cl = o / ND, syi = o - cl * ND;  // slot 8 quarter + cl, sy = syi - R
-            // lane 4 cl + i holds row i of the slot; its column for sy is i + R - sy
-            const float *e = eb + (TC_ROWS * cl) * TC_EB_PITCH + (2 * R - syi);
-            float s = e[0];
-            s += e[TC_EB_PITCH + 1];
-            s += e[2 * TC_EB_PITCH + 2];
-            s += e[3 * TC_EB_PITCH + 3];
-            pw[syi * ND + 8 * quarter + cl] = s;
-        }
-        __syncwarp();
+    for (int o = lane; o < nout; o += 32) {
+        const int cl = o / ND, syi = o - cl * ND;  // slot 8 quarter + cl, sy = syi - R
+        // lane 4 cl + i holds row i of the slot; its column for sy is i + R - sy
+        const float *e = eb + (TC_ROWS * cl) * TC_EB_PITCH + (2 * R - syi);
+        float s = e[0];
+        s += e[TC_EB_PITCH + 1];
+        s += e[2 * TC_EB_PITCH + 2];
+        s += e[3 * TC_EB_PITCH + 3];
+        pw[syi * ND + 8 * quarter + cl] = s;
     }
+    __syncwarp();
 }
 
-// --------------------------------------------------------------- planes --
+// ------------------------------------------------- the tensor-core phase --
 
-// Planes of every window of the tile into Ps (NP floats per window), window
-// row by window row.  Returns false (error word set, MMAs in flight drained
-// with a bounded wait) if a wait gave up.
+// Barriers of the phase (after the region load's barrier):
+//   full[NS]      a producer warp filled a ring slot (group k is built by
+//                 producer warp k mod TC_PRODUCERS, whole)
+//   empty[NS]     the MMAs that read a slot completed (commit)
+//   slab_full[2]  producer warps built a row's slab
+//   row_done[2]   a row's MMAs completed (commit): its slab is free, its TMEM
+//                 block ready for the epilogue
+//   tmem_free[2]  the epilogue warps read a row's TMEM block (one arrival each)
+constexpr int TC_PRODUCERS = 4;  // producer warps: 2, 5, 6, 7
+constexpr int TC_EPI_WARPS = 3;  // epilogue warps: 0, 4 (lane quarter 0), 1 (quarter 1)
+constexpr int TC_ISSUER = 3;     // warp of the MMA-issuing thread
+
+__device__ __forceinline__ int tc_producer_index(int warp)
+{
+    return warp == 2 ? 0 : (warp >= 5 ? warp - 4 : -1);
+}
+
 template <int PREC, int GC>
-static __device__ __forceinline__ bool tc_planes(const PassArgs &a, const TileGeom &g, const float *As,
-                                                 const float *Bs, float *Ps, unsigned char *smem, uint32_t tmem,
-                                                 uint64_t *mbar, float m)
+static __device__ __forceinline__ void tc_phase(const PassArgs &a, const TileGeom &g, const float *As,
+                                                const float *Bs, float *Ps, unsigned char *smem, uint32_t tmem,
+                                                uint64_t *bars, float m, volatile int *abort)
 {
     constexpr int R = TC_R, W = 2 * GC, NG = (W + 2 * R) / TC_ROWS, KS = W / 16, CPW = GC / 8;
+    constexpr int NP = (2 * R + 1) * (2 * R + 1);
     static_assert((W + 2 * R) % TC_ROWS == 0 && GC % 8 == 0, "shape");
     const PassPlan &P = a.plan;
-    const int tid = threadIdx.x;
-    const int nbuf = P.tc_nbuf;
-    unsigned char *slab = smem + P.off_slab;
-    float *ebuf = reinterpret_cast<float *>(smem + P.off_ebuf);
-    const uint32_t slab_s = smem_addr(slab), cp_s = smem_addr(smem + P.off_cp);
-    const uint32_t idesc = tc_idesc<PREC>();
-    // per buffer: commits issued and waited (parity of the next wait = waited & 1)
-    uint32_t issued_mask = 0;  // buffers with a commit not yet waited for
-    uint32_t waited = 0;       // bit b: parity of buffer b's next wait
-    int step = 0;
-    // test hook: wait on a phase of the first buffer's barrier that no commit
-    // completes, before any MMA is issued (the wait runs out with nothing in flight)
-    if (a.dbg_stall == 2 && !tc_cta_wait(a, mbar, 0u)) goto drain;
-    for (int wy = 0; wy < g.nwy; ++wy) {
-        tc_build_slab<PREC>(P, g, As, slab, wy, m);
-        for (int gi = 0; gi < NG; ++gi, ++step) {
-            const int b = step % nbuf;
-            if (issued_mask & (1u << b)) {
-                // the MMAs that read this buffer last must have completed
-                if (!tc_cta_wait(a, mbar + b, (waited >> b) & 1u)) goto drain;
-                waited ^= 1u << b;
-                issued_mask &= ~(1u << b);
-            }
-            tc_build_group<PREC>(P, g, Bs, smem + P.off_cp + b * P.cp_bytes, wy, gi, m);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = P.tc_nbuf;
+    uint64_t *full = bars, *empty = bars + NS, *slab_full = bars + 2 * NS, *row_done = slab_full + 2,
+             *tmem_free = row_done + 2;
+    unsigned char *slab = smem + P.off_slab;  // two slabs, slab_bytes apart
+    unsigned char *ring = smem + P.off_cp;
+    const int slab_bytes = P.slab_lbo * (g.aw >> 3);
+    const int tcols = 16 * P.TX;  // columns of one row's TMEM block
+    const int pidx = tc_producer_index(warp);
+
+    if (pidx >= 0) {
+        // ---------------------------------------------------------- producers
+        const int t = pidx * 32 + lane, nt = TC_PRODUCERS * 32;
+        for (int wy = 0; wy < g.nwy; ++wy) {
+            const int sb = wy & 1;
+            if (wy >= 2 && !warp_wait(a, row_done + sb, ((wy >> 1) - 1) & 1, abort)) return;
+            tc_slab<PREC>(P, g, As, slab + sb * slab_bytes, wy, m, t, nt);
             fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint64_t da0 = tc_desc(cp_s + b * P.cp_bytes, P.cp_lbo, 128);
-                const uint64_t db0 = tc_desc(slab_s + TC_ROWS * gi * 16, P.slab_lbo, 128);
-                for (int wx = 0; wx < g.nwx; ++wx) {
-#pragma unroll
-                    for (int kk = 0; kk < KS; ++kk) {
-                        const int chunk = wx * CPW + 2 * kk;
-                        // the start-address field is the low 14 bits, in units of 16 bytes
-                        tc_mma(tmem + (uint32_t)(16 * wx), da0 + (uint64_t)((chunk * P.cp_lbo) >> 4),
-                               db0 + (uint64_t)((chunk * P.slab_lbo) >> 4), idesc, (gi | kk) != 0 ? 1u : 0u);
-                    }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(slab_full + sb);
+            for (int gi = 0; gi < NG; ++gi) {
+                const int k = wy * NG + gi, slot = k % NS;
+                if (k % TC_PRODUCERS != pidx) continue;
+                if (k >= NS && !warp_wait(a, empty + slot, ((k / NS) - 1) & 1, abort)) return;
+                tc_group<PREC>(P, g, Bs, ring + slot * P.cp_group, wy, gi, m, lane, 32);
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full + slot);
+            }
+        }
+    } else if (warp == TC_ISSUER) {
+        // ------------------------------------------------------------- issuer
+        const uint32_t idesc = tc_idesc<PREC>();
+        const uint32_t slab_s = smem_addr(slab), ring_s = smem_addr(ring);
+        uint64_t *last = nullptr;  // the barrier of the last commit, and its phase
+        uint32_t last_par = 0;
+        bool ok = true;
+        for (int wy = 0; wy < g.nwy && ok; ++wy) {
+            const int tb = wy & 1;
+            if (wy >= 2 && !warp_wait(a, tmem_free + tb, ((wy >> 1) - 1) & 1, abort)) {
+                ok = false;
+                break;
+            }
+            if (!warp_wait(a, slab_full + tb, (wy >> 1) & 1, abort)) {
+                ok = false;
+                break;
+            }
+            for (int gi = 0; gi < NG; ++gi) {
+                const int k = wy * NG + gi, slot = k % NS;
+                if (!warp_wait(a, full + slot, (k / NS) & 1, abort)) {
+                    ok = false;
+                    break;
                 }
-                tc_commit(mbar + b);
+                if (lane == 0) {
+                    tc_fence_after();
+                    // the start-address field is the low 14 bits, in units of 16 bytes
+                    const uint64_t da0 = tc_desc(ring_s + slot * P.cp_group, P.cp_lbo, 128);
+                    const uint64_t db0 = tc_desc(slab_s + tb * slab_bytes + TC_ROWS * gi * 16, P.slab_lbo, 128);
+                    for (int wx = 0; wx < g.nwx; ++wx) {
+#pragma unroll
+                        for (int kk = 0; kk < KS; ++kk) {
+                            const int chunk = wx * CPW + 2 * kk;
+                            tc_mma(tmem + (uint32_t)(tb * tcols + 16 * wx), da0 + (uint64_t)((chunk * P.cp_lbo) >> 4),
+                                   db0 + (uint64_t)((chunk * P.slab_lbo) >> 4), idesc, (gi | kk) != 0 ? 1u : 0u);
+                        }
+                    }
+                    tc_commit(empty + slot);
+                }
+                last = empty + slot;
+                last_par = (k / NS) & 1;
             }
-            issued_mask |= 1u << b;
+            if (!ok) break;
+            if (lane == 0) tc_commit(row_done + tb);
+            last = row_done + tb;
+            last_par = (wy >> 1) & 1;
         }
-        // every MMA of the row has completed once each pending commit has
-        for (int b = 0; b < nbuf; ++b)
-            if (issued_mask & (1u << b)) {
-                if (!tc_cta_wait(a, mbar + b, (waited >> b) & 1u)) goto drain;
-                waited ^= 1u << b;
-                issued_mask &= ~(1u << b);
-            }
-        tc_fence_after();
-        tc_epilogue(g, tmem, ebuf, Ps, wy);
-        // TMEM columns and the slab are rewritten by the next row
-        tc_fence_before();
-        __syncthreads();
+        if (!ok && last && lane == 0) {
+            // drain: a bounded chance for the MMAs in flight before TMEM is freed
+            const int lim = a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT;
+            for (int it = 0; it < lim; ++it)
+                if (mbar_try_wait(last, last_par)) break;
+        }
+        __syncwarp();
+    } else if (warp == 0 || warp == 1 || warp == 4) {
+        // ----------------------------------------------------------- epilogue
+        const int quarter = warp & 3;
+        float *eb = reinterpret_cast<float *>(smem + P.off_ebuf) + (warp == 4 ? 2 : quarter) * 32 * TC_EB_PITCH;
+        for (int wy = 0; wy < g.nwy; ++wy) {
+            const int tb = wy & 1;
+            if (!warp_wait(a, row_done + tb, (wy >> 1) & 1, abort)) return;
+            tc_fence_after();
+            // quarter 0: warps 0 and 4 take alternate windows; quarter 1: warp 1 all
+            const int wx0 = warp == 4 ? 1 : 0, dwx = quarter == 0 ? 2 : 1;
+            for (int wx = wx0; wx < g.nwx; wx += dwx)
+                tc_epilogue_window(tmem, quarter, (uint32_t)(tb * tcols + 16 * wx), eb,
+                                   Ps + (wy * g.nwx + wx) * NP);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_free + tb);
+        }
     }
-    return true;
-drain:
-    // a second bounded chance for the MMAs in flight before the caller frees TMEM
-    for (int b = 0; b < nbuf; ++b)
-        if (issued_mask & (1u << b)) {
-            if (threadIdx.x < 32)
-                for (int it = 0; it < (a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT); ++it)
-                    if (mbar_try_wait(mbar + b, (waited >> b) & 1u)) break;
-        }
-    __syncthreads();
-    return false;
 }
 
-// One warp per window: the scaled coefficient from the window's plane in
-// offset form, (P - (mu_A - m)(S1 - n m)) / sqrt(E_B), which equals the
-// numerator sum (A - mu_A) B' of the definition; argmax with ties to the
-// smallest row-major index; all five stencil points go to the FP32 refit.
+// ------------------------------------------------- FP32 refit planes --
+
+// Block planes of the FP32 refit: Q_b(s) = sum over block b of A(x) B'(x + s)
+// for |sy|, |sx| <= TC_RN (the stencil of every peak within one pixel of the
+// predictor), from the FP32 regions staged for radius R.  Each thread owns one
+// (block, sy, row group) and keeps the 2 TC_RN + 1 sx accumulators in
+// registers (as block_planes_fp32), RG row groups summed by shuffles.
+static __device__ __forceinline__ void tc_refit_planes(const PassArgs &a, const TileGeom &g, const float *As,
+                                                       const float *Bs, float *Qs)
+{
+    constexpr int RN = TC_RN, ND = 2 * RN + 1;
+    constexpr int MIS = ((-RN) % 4 + 4) % 4;
+    constexpr int NQ = (4 + 2 * RN + MIS + 3) / 4;
+    const PassPlan &P = a.plan;
+    const int G = g.G, RG = P.RGx, rows = G / RG, lrg = __ffs(RG) - 1;
+    const int units = g.nb * ND;  // (block, sy)
+    const int lane = threadIdx.x & 31, gi = lane >> (5 - lrg), ul = lane & ((32 >> lrg) - 1);
+    // B' row of A row y at shift sy: smem row y + sy + R + 1, with sy = syi - RN
+    const int row_off = g.R + 1 - RN;
+    for (int base = (threadIdx.x - lane) >> lrg; base < units; base += blockDim.x >> lrg) {
+        const int u = min(base + ul, units - 1);
+        const int b = u / ND, syi = u - b * ND;
+        const int byi = b / g.nbx, bxi = b - byi * g.nbx;
+        const int c0 = bxi * G, r0 = byi * G + gi * rows;
+        float acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = 0.f;
+        for (int y = r0; y < r0 + rows; ++y) {
+            const float *arow = As + y * P.a_pitch;
+            const float *brow = Bs + (y + syi + row_off) * P.b_pitch + P.padl - RN - MIS;
+            for (int c = c0; c < c0 + G; c += 4) {
+                const float4 a4 = *reinterpret_cast<const float4 *>(arow + c);
+                float bv[NQ * 4];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 t = *reinterpret_cast<const float4 *>(brow + c + 4 * q);
+                    bv[4 * q] = t.x;
+                    bv[4 * q + 1] = t.y;
+                    bv[4 * q + 2] = t.z;
+                    bv[4 * q + 3] = t.w;
+                }
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d] = fmaf(av[j], bv[MIS + j + d], acc[d]);
+                }
+            }
+        }
+        sum_row_groups<ND>(acc, lrg);
+        if (base + ul < units && gi == 0) {
+            float *out = Qs + b * ND * ND + syi * ND;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) out[d] = acc[d];
+        }
+    }
+}
+
+// One warp per window: the scaled coefficient from the window's tensor-core
+// plane in offset form, (P - (mu_A - m)(S1 - n m)) / sqrt(E_B), which equals
+// the numerator sum (A - mu_A) B' of the definition; argmax with ties to the
+// smallest row-major index.  A peak within one pixel of the predictor takes
+// its five stencil values from the FP32 refit planes (the window's four
+// blocks); the others go to the direct FP32 sums.
 static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps,
-                                                         const float *Vs, const float *stats, float m,
-                                                         const WinShared &ws)
+                                                         const float *Qs, const float *Vs, const float *stats,
+                                                         float m, const WinShared &ws)
 {
     constexpr int R = TC_R, ND = 2 * R + 1, NP = ND * ND, NQ = (NP + 31) / 32;
+    constexpr int RN = TC_RN, NDN = 2 * RN + 1;
     constexpr uint32_t NONE = 0xffffffffu;
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -373,9 +506,25 @@ static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, cons
         const uint32_t key = bq == NONE ? 0u : ord_key(best);
         const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
         const uint32_t qmin = __reduce_min_sync(0xffffffffu, (key == kmax && bq != NONE) ? bq : NONE);
+        const int bidx = qmin < (uint32_t)NP ? (int)qmin : NP / 2;  // no finite value: zero shift
+        const int ky = bidx / ND - R, kx = bidx % ND - R;
+        const bool near = ky >= 1 - RN && ky <= RN - 1 && kx >= 1 - RN && kx <= RN - 1;
+        if (near && lane < 5) {
+            int sy, sx;
+            stencil_shift(lane, ky, kx, sy, sx);
+            // blocks (wyi + yy, wxi + xx) of the window (50 % overlap: 2 x 2 blocks)
+            const float *q0 = Qs + (wyi * g.nbx + wxi) * NDN * NDN + (sy + RN) * NDN + (sx + RN);
+            const int rs = g.nbx * NDN * NDN;
+            float num = q0[0];
+            num += q0[NDN * NDN];
+            num += q0[rs];
+            num += q0[rs + NDN * NDN];
+            const int vo = sy * cp + sx;
+            ws.c5[wi * 5 + lane] = scaled_zncc(num, muA, v1[vo], vn[vo]);
+        }
         if (lane == 0) {
-            ws.peaks[wi] = qmin < (uint32_t)NP ? (int)qmin : NP / 2;  // no finite value: zero shift
-            ws.need[wi] = 0x1f;
+            ws.peaks[wi] = bidx;
+            ws.need[wi] = near ? 0 : 0x1f;
         }
     }
 }
@@ -383,8 +532,8 @@ static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, cons
 // ------------------------------------------------------------- the kernel --
 
 // Tiles of TX x TY windows of 50 % overlap (w = 2 GC, s = GC), r = 4: regions,
-// FP32 statistics and box sums as in pass_kernel, tensor-core planes per window
-// row, argmax on the planes, FP32 five-point refit, Gaussian fit.
+// FP32 statistics and box sums as in pass_kernel, the FP32 refit planes, the
+// tensor-core phase, argmax on the planes, the refit, the Gaussian fit.
 template <int PREC, int GC>
 __global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const PassArgs a)
 {
@@ -424,13 +573,16 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const PassArgs
     float *Cs = reinterpret_cast<float *>(smem + P.off_h);
     float *Vs = reinterpret_cast<float *>(smem + P.off_v);
     float *Ps = reinterpret_cast<float *>(smem + P.off_p);
+    float *Qs = reinterpret_cast<float *>(smem + P.off_refit);  // FP32 refit planes
     float *stats = reinterpret_cast<float *>(smem + P.off_stats);
     float2 *bst = reinterpret_cast<float2 *>(smem + P.off_gst);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + P.off_red);  // [0]: regions, [1..]: MMA buffers
-    // after the barriers: the TMEM address and the tile offset (no static
-    // shared memory, so that the full dynamic carve-out can be granted)
-    uint32_t &tmem_slot = *reinterpret_cast<uint32_t *>(bar + 1 + P.tc_nbuf);
-    float &tile_off = *(reinterpret_cast<float *>(bar + 1 + P.tc_nbuf) + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + P.off_red);  // [0]: regions, then the phase's
+    const int nbars = 2 * P.tc_nbuf + 6;
+    // after the barriers: the TMEM address, the tile offset and the abort flag
+    // (no static shared memory, so that the full dynamic carve-out can be granted)
+    uint32_t &tmem_slot = *reinterpret_cast<uint32_t *>(bar + 1 + nbars);
+    float &tile_off = *(reinterpret_cast<float *>(bar + 1 + nbars) + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(bar + 2 + nbars);
     WinShared ws;
     ws.c5 = reinterpret_cast<float *>(smem + P.off_c5);
     ws.peaks = reinterpret_cast<int *>(smem + P.off_peaks);
@@ -445,8 +597,19 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const PassArgs
         return;
     }
     if (warp == 0) tc_alloc(&tmem_slot, P.tmem_cols);
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < P.tc_nbuf; ++b) mbar_init(bar + 1 + b, 1);
+    if (threadIdx.x == 32) {
+        const int NS = P.tc_nbuf;
+        for (int b = 0; b < NS; ++b) {
+            mbar_init(bar + 1 + b, 1);              // full (one producer warp)
+            mbar_init(bar + 1 + NS + b, 1);         // empty (commit)
+        }
+        mbar_init(bar + 1 + 2 * NS, TC_PRODUCERS);  // slab_full
+        mbar_init(bar + 2 + 2 * NS, TC_PRODUCERS);
+        mbar_init(bar + 3 + 2 * NS, 1);             // row_done (commit)
+        mbar_init(bar + 4 + 2 * NS, 1);
+        mbar_init(bar + 5 + 2 * NS, TC_EPI_WARPS);  // tmem_free
+        mbar_init(bar + 6 + 2 * NS, TC_EPI_WARPS);
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
 
@@ -462,26 +625,32 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const PassArgs
         sum = warp_sum(sum);
         if (lane == 0) tile_off = sum / (float)(g.aw * g.ah);
     }
-    fence_proxy_async();
+    // 3: FP32 refit planes (their buffer is not reused by the tensor-core phase)
+    tc_refit_planes(a, g, As, Bs, Qs);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const float m = tile_off;
 
-    // 3: tensor-core planes (operand buffers over the dead C region)
-    const bool ok = tc_planes<PREC, GC>(a, g, As, Bs, Ps, smem, tmem, bar + 1, m);
+    // 4: tensor-core planes (operand buffers over the dead column box sums)
+    if (a.dbg_stall == 2 && warp == TC_ISSUER) {
+        // test hook: wait on a phase of the first slot's barrier that nothing
+        // completes, before any MMA is issued
+        warp_wait(a, bar + 1 + P.tc_nbuf, 0u, abort);
+    }
+    tc_phase<PREC, GC>(a, g, As, Bs, Ps, smem, tmem, bar + 1, m, abort);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tc_dealloc(tmem, P.tmem_cols);
-    if (!ok) {
+    if (*abort) {
         invalid_tile(a, g, pair);
         return;
     }
 
-    // 4: argmax on the planes, FP32 five-point refit, Gaussian fit, outputs
-    tc_plane_and_peak(a, g, Ps, Vs, stats, m, ws);
+    // 5: argmax on the planes, FP32 five-point refit, Gaussian fit, outputs
+    tc_plane_and_peak(a, g, Ps, Qs, Vs, stats, m, ws);
     __syncthreads();
     stencil_direct(a, g, As, Bs, ws);
     __syncthreads();

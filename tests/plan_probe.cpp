@@ -4,7 +4,7 @@
 // "w s R nx ny prec" lines on stdin and prints one line per case:
 //   ok TX TY tiles_x tiles_y smem RGx lv lh nv nh | sTX srows stiles_x stiles_y ssmem slv slh snv snh
 //   | tc off_p off_red off_gst off_h off_slab slab_rows slab_lbo off_cp cp_bytes cp_lbo nbuf off_ebuf tmem_cols
-//     off_c5 off_dpart
+//     off_c5 off_dpart cp_group off_refit
 #include <cstdio>
 
 #include "rpiv_internal.h"
@@ -42,9 +42,9 @@ int main()
                     p.tiles_x, p.tiles_y, p.smem_bytes, p.RGx, p.box_lv, p.box_lh, p.box_nv, p.box_nh, st.TX,
                     st.strip_rows, st.tiles_x, st.tiles_y, st.smem_bytes, st.box_lv, st.box_lh, st.box_nv,
                     st.box_nh);
-        std::printf(" | %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", p.tc, p.off_p, p.off_red, p.off_gst,
-                    p.off_h, p.off_slab, p.slab_rows, p.slab_lbo, p.off_cp, p.cp_bytes, p.cp_lbo, p.tc_nbuf,
-                    p.off_ebuf, p.tmem_cols, p.off_c5, p.off_dpart);
+        std::printf(" | %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", p.tc, p.off_p, p.off_red,
+                    p.off_gst, p.off_h, p.off_slab, p.slab_rows, p.slab_lbo, p.off_cp, p.cp_bytes, p.cp_lbo,
+                    p.tc_nbuf, p.off_ebuf, p.tmem_cols, p.off_c5, p.off_dpart, p.cp_group, p.off_refit);
     }
     return 0;
 }

@@ -71,8 +71,9 @@ def test_batch_of_distinct_pairs_equals_pairs_one_by_one():
     eng.close()
 
 
-@pytest.mark.parametrize("stall,precision", [(1, "fp32"), (1, "bf16"), (2, "bf16")])
-def test_stage_bounded_wait_runs_out_and_is_reported(stall, precision, monkeypatch):
+@pytest.mark.parametrize("stall,precision,tc", [(1, "fp32", "0"), (1, "bf16", "0"), (1, "bf16", "1"),
+                                               (2, "bf16", "1")])
+def test_stage_bounded_wait_runs_out_and_is_reported(stall, precision, tc, monkeypatch):
     """A stage kernel's bounded wait made to run out (the test hook waits on a
     barrier phase that nothing completes, after the region copies have landed
     or before any MMA is issued): the call itself succeeds, its windows are
@@ -84,6 +85,7 @@ def test_stage_bounded_wait_runs_out_and_is_reported(stall, precision, monkeypat
     nx, ny = (256 - 16) // 8 + 1, (224 - 16) // 8 + 1
     pu = torch.full((ny, nx), 12.0, device="cuda:0")
     pv = torch.full((ny, nx), -0.5, device="cuda:0")
+    monkeypatch.setenv("RPIV_TC_PLANES", tc)  # 1: the tcgen05 kernel (stall 2 waits on its MMA barrier)
     rp.stage_status()  # start from a clear word
     monkeypatch.setenv("RPIV_DEBUG_STALL", str(stall))
     u, v, info = rp.stage_correlate(a, b, 16, 8, 4, pu, pv, precision=precision)

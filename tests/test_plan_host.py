@@ -39,11 +39,12 @@ def probe(tmp_path_factory):
     subprocess.run([cxx, "-std=c++17", "-O1", "-I", inc, "-I", CSRC, os.path.join(ROOT, "tests", "plan_probe.cpp"),
                     os.path.join(CSRC, "pass_plan.cpp"), "-o", exe], check=True, capture_output=True, text=True)
     env = {k: v for k, v in os.environ.items()
-           if k not in ("RPIV_MIN_CTAS", "RPIV_TILE_SMEM_KB", "RPIV_PLANE_ITEMS", "RPIV_STRIP_ROWS")}
+           if k not in ("RPIV_MIN_CTAS", "RPIV_TILE_SMEM_KB", "RPIV_PLANE_ITEMS", "RPIV_STRIP_ROWS", "RPIV_TC_PLANES")}
 
-    def run(cases):
+    def run(cases, extra_env=None):
         text = "".join(f"{w} {s} {R} {nx} {ny} {p}\n" for (w, s, R, nx, ny, p) in cases)
-        out = subprocess.run([exe], input=text, check=True, capture_output=True, text=True, env=env).stdout
+        out = subprocess.run([exe], input=text, check=True, capture_output=True, text=True,
+                             env={**env, **(extra_env or {})}).stdout
         res = []
         for line in out.strip().splitlines():
             a, b, c = line.split("|")
@@ -53,7 +54,8 @@ def probe(tmp_path_factory):
                             strip=dict(TX=st[0], rows=st[1], tiles_x=st[2], tiles_y=st[3], smem=st[4], lv=st[5],
                                        lh=st[6], nv=st[7], nh=st[8]),
                             tc=dict(zip(("tc off_p off_red off_gst off_h off_slab slab_rows slab_lbo off_cp cp_bytes "
-                                         "cp_lbo nbuf off_ebuf tmem_cols off_c5 off_dpart").split(), tc))))
+                                         "cp_lbo nbuf off_ebuf tmem_cols off_c5 off_dpart cp_group off_refit").split(),
+                                        tc))))
         assert len(res) == len(cases)
         return res
     return run
@@ -135,17 +137,17 @@ def test_the_16px_pass_of_the_1mp_workload_takes_longer_box_runs(probe):
 def test_tensor_core_tiles_keep_every_operand_read_inside_shared_memory(probe):
     """tcgen05 tiles (16-bit, 50 % overlap with 8/16/32 px steps, r = 4): the
     MMA operands are read through descriptors, so every address an MMA can form
-    must lie in the tile's shared memory.  A copy buffer's MMAs reach 2048 -
-    (2R + 1) 64 bytes past its last chunk (unused shift slots), the slab's reach
-    (2R above to 16 - 4 below the window) must stay in the slab, and the TMEM
-    columns must cover 16 per window with at most 512 per SM at the occupancy
-    the shared memory allows."""
+    must lie in the tile's shared memory.  A copy buffer's MMAs reach past the
+    last group's chunks (the unused shift slots) and must stay in the buffer,
+    the slab's reach (2R above to 16 - 4 below the window) must stay in the
+    slab, and the TMEM columns must cover 16 per window with at most 512 per SM
+    at the occupancy the shared memory allows."""
     cases = []
     for s in (8, 16, 32):
         for prec in (1, 2):
             for nx, ny in [(1, 1), (2, 3), (7, 5), (31, 31), (127, 127), (63, 9), (159, 89), (11, 255)]:
                 cases.append((2 * s, s, 4, nx, ny, prec))
-    res = probe(cases)
+    res = probe(cases, {"RPIV_TC_PLANES": "1"})
     R, rows = 4, 4
     for (w, s, _, nx, ny, prec), r in zip(cases, res):
         t = r["tc"]
@@ -154,22 +156,27 @@ def test_tensor_core_tiles_keep_every_operand_read_inside_shared_memory(probe):
         assert smem <= SMEM_MAX
         aw, ah = (TX - 1) * s + w, (TY - 1) * s + w
         nch, ng = aw // 8, (w + 2 * R) // rows
-        assert t["cp_lbo"] == (2 * R + 1) * rows * 16 and t["cp_bytes"] == nch * t["cp_lbo"]
-        assert 2 <= t["nbuf"] <= ng
-        # every address the copies' MMAs can form, for the last buffer, the last window, the last K step
-        reach = t["off_cp"] + (t["nbuf"] - 1) * t["cp_bytes"] + (nch - 1) * t["cp_lbo"] + 2048
-        assert reach <= smem, (w, TX, TY, reach, smem)
-        # the slab: rows 4 g + n of every group, both K chunks of the last window
+        assert t["cp_lbo"] == 8 * rows * 16 and t["cp_group"] == (nch + 1) * t["cp_lbo"]
+        assert t["nbuf"] in (4, 6) and t["cp_bytes"] >= t["nbuf"] * t["cp_group"]
+        # every address the copies' MMAs can form: the last slot of the ring, the
+        # last window's last K step (chunk nch - 2), every M row (16 slots of 4 rows
+        # past it) and both K chunks; it must stay in the ring
+        start = t["off_cp"] + (t["nbuf"] - 1) * t["cp_group"] + (nch - 2) * t["cp_lbo"]
+        reach = start + 7 * 16 + 15 * 128 + 7 * 2 + t["cp_lbo"] + 2
+        assert reach <= t["off_cp"] + t["cp_bytes"], (w, TX, TY)
+        # the slabs (two rows): rows 4 g + n of every group, both K chunks of the last window
         assert rows * (ng - 1) + 16 <= t["slab_rows"]
-        assert t["off_slab"] + nch * t["slab_lbo"] <= t["off_cp"]
-        assert t["off_cp"] + t["nbuf"] * t["cp_bytes"] <= t["off_ebuf"]
-        assert t["off_ebuf"] + 4 * 32 * 20 * 4 <= smem
-        # the buffers over the dead column sums start after the planes, which persist
-        assert t["off_p"] + TX * TY * (2 * R + 1) ** 2 * 4 <= t["off_h"] == t["off_slab"] == t["off_c5"]
-        assert t["off_red"] + 8 * (1 + t["nbuf"]) + 8 <= t["off_gst"]
-        for k in ("off_p", "off_red", "off_slab", "off_cp", "off_ebuf", "cp_bytes", "slab_lbo"):
+        assert t["off_slab"] + 2 * nch * t["slab_lbo"] <= t["off_cp"]
+        assert t["off_cp"] + t["cp_bytes"] <= t["off_ebuf"]
+        assert t["off_ebuf"] + 3 * 32 * 20 * 4 <= smem
+        # persistent buffers (planes, refit planes) precede the reused region
+        nb = (aw // s) * (ah // s)
+        assert t["off_p"] + TX * TY * (2 * R + 1) ** 2 * 4 <= t["off_refit"]
+        assert t["off_refit"] + nb * 25 * 4 <= t["off_h"] == t["off_slab"] == t["off_c5"]
+        assert t["off_red"] + 8 * (1 + 2 * t["nbuf"] + 6) + 16 <= t["off_gst"]
+        for k in ("off_p", "off_red", "off_slab", "off_cp", "off_ebuf", "cp_bytes", "slab_lbo", "off_refit"):
             assert t[k] % 16 == 0, k
         cols = t["tmem_cols"]
-        assert cols >= max(32, 16 * TX) and cols & (cols - 1) == 0 and cols <= 512
+        assert cols >= max(32, 32 * TX) and cols & (cols - 1) == 0 and cols <= 512
         ctas = min(228 * 1024 // (smem + 1024), 2048 // THREADS)
-        assert ctas * cols <= 512 or 512 // cols >= 2
+        assert min(ctas, 512 // cols) >= 1
