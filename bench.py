@@ -60,6 +60,11 @@ def parse():
     p.add_argument("--streams", type=int, default=32)
     p.add_argument("--load", type=float, default=0.7, help="Poisson rate as a fraction of the saturation rate")
     p.add_argument("--extra-loads", default="0.5", help="further load fractions reported beside --load (serve mode)")
+    p.add_argument("--serve-precision", default="fp32", choices=["fp32", "bf16", "fp16"],
+                   help="correlation precision of the serving mix")
+    p.add_argument("--serve-compare", default="", help="further precisions measured in the serving mix, e.g. bf16")
+    p.add_argument("--slots", type=int, default=4, help="concurrent batches (CUDA streams) in the serving mix")
+    p.add_argument("--repeats", type=int, default=3, help="Poisson runs at --load with fresh arrival seeds")
     return p.parse_args()
 
 
@@ -138,12 +143,15 @@ def _render_stream(args):
 
 def run_serve(args):
     """Streaming mix: camera streams of 512^2 .. 3840x2160, u8 or 12-bit,
-    previous field as predictor, BF16 correlation, at most 64 pairs per
-    launch, 40 GB admission budget; saturation throughput, then Poisson
-    arrivals at a fraction of it with p50/p99 latency."""
+    previous field as predictor, at most 64 pairs per launch, 40 GB admission
+    budget; saturation throughput, then Poisson arrivals at a fraction of it
+    with p50/p99 latency, repeated with fresh arrival seeds.  The mix runs in
+    the faster correlation precision (FP32) unless told otherwise; further
+    precisions are measured the same way and reported beside it."""
     import synth
     from synth import workloads as wl
     ring = 4
+    slots = args.slots
     rnd = synth.uniform(777, 2 * args.streams)
     cum = np.cumsum([w for _, _, w in wl.SERVING_SIZES])
     streams = []
@@ -173,20 +181,50 @@ def run_serve(args):
                                   payload=pinned[s][f % ring]))
         return out
 
-    ex = sv.GpuExecutor(slots=4, precision="bf16", max_batch=64, cold_batch=8, prewarm=True)
-    # every engine (frame size, mode, slot) and every batch size's graph exist before any timing
-    for key in sorted({(W, H, bits) for _, W, H, bits, _ in streams}):
-        for mode in (sv.COLD, sv.WARM):
-            for slot in range(4):
-                ex._engine(key, mode, slot)
-    torch.cuda.synchronize()
-    # saturation: every request available at once (also warms engines and graphs)
-    n_sat = min(args.requests, 2000)
-    sat = sv.Scheduler(ex, max_batch=64, slots=4, hbm_budget=40e9).run(requests(n_sat, 0.0, 1), realtime=False)
-    rate = args.load * sat["pairs_per_s"]
-    torch.cuda.synchronize()
-    sch = sv.Scheduler(ex, max_batch=64, slots=4, hbm_budget=40e9)
-    rep = sch.run(requests(args.requests, rate, 2))
+    def scheduler(ex):
+        return sv.Scheduler(ex, max_batch=64, slots=slots, hbm_budget=40e9)
+
+    def summary(sch, rep):
+        wait = [1000.0 * (r.dispatched - r.arrival) for r in sch.done]
+        service = [1000.0 * (r.done - r.dispatched) for r in sch.done]
+        return {"pairs_per_s": rep["pairs_per_s"], "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
+                "max_ms": rep["max_ms"], "mean_batch": rep["mean_batch"],
+                "queue_p50_ms": float(np.percentile(wait, 50)), "queue_p99_ms": float(np.percentile(wait, 99)),
+                "service_p50_ms": float(np.percentile(service, 50)),
+                "service_p99_ms": float(np.percentile(service, 99)),
+                "host_busy_frac": rep["host_busy_frac"], "host_us_per_batch": rep["host_us_per_batch"]}
+
+    def measure(precision, repeats):
+        ex = sv.GpuExecutor(slots=slots, precision=precision, max_batch=64, cold_batch=8, prewarm=True)
+        # every engine (frame size, mode, slot) and every batch size's graph exist before any timing
+        for key in sorted({(W, H, bits) for _, W, H, bits, _ in streams}):
+            for mode in (sv.COLD, sv.WARM):
+                for slot in range(slots):
+                    ex._engine(key, mode, slot)
+        torch.cuda.synchronize()
+        # saturation: every request available at once (also warms engines and graphs)
+        n_sat = min(args.requests, 2000)
+        sat_s = scheduler(ex)
+        sat = sat_s.run(requests(n_sat, 0.0, 1), realtime=False)
+        rate = args.load * sat["pairs_per_s"]
+        torch.cuda.synchronize()
+        runs = []
+        for rep_i in range(repeats):
+            sch = scheduler(ex)
+            rep = sch.run(requests(args.requests, rate, 2 + rep_i))
+            runs.append((sch, rep))
+        others = {}
+        for frac in [float(x) for x in args.extra_loads.split(",") if x.strip()]:
+            sch = scheduler(ex)
+            r2 = sch.run(requests(args.requests, frac * sat["pairs_per_s"], 100 + int(100 * frac)))
+            others[str(frac)] = dict(summary(sch, r2), arrival_rate_per_s=frac * sat["pairs_per_s"])
+        ex.close()
+        return sat, rate, runs, others
+
+    sat, rate, runs, others = measure(args.serve_precision, max(1, args.repeats))
+    # the run with the median p99 is the headline; every run is listed
+    order = sorted(range(len(runs)), key=lambda i: runs[i][1]["p99_ms"])
+    sch, rep = runs[order[len(order) // 2]]
     by_size = {}
     for r in sch.done:
         by_size.setdefault(f"{r.key[0]}x{r.key[1]}", []).append(1000.0 * r.latency)
@@ -195,28 +233,30 @@ def run_serve(args):
     steady = sorted(1000.0 * r.latency for r in sch.done if r.frame >= 3 and r.error is None)
     steady_p = {"p50_ms": float(np.percentile(steady, 50)), "p99_ms": float(np.percentile(steady, 99)),
                 "what": "requests after each stream's first three frames (start-up transient excluded)"}
-    wait = [1000.0 * (r.dispatched - r.arrival) for r in sch.done]
-    service = [1000.0 * (r.done - r.dispatched) for r in sch.done]
-    split = {"queue_p50_ms": float(np.percentile(wait, 50)), "queue_p99_ms": float(np.percentile(wait, 99)),
-             "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99))}
+    s = summary(sch, rep)
+    split = {k: s[k] for k in ("queue_p50_ms", "queue_p99_ms", "service_p50_ms", "service_p99_ms")}
+    p99s = [r[1]["p99_ms"] for r in runs]
+    compare = {}
+    for prec in [x.strip() for x in args.serve_compare.split(",") if x.strip() and x.strip() != args.serve_precision]:
+        sat2, rate2, runs2, _ = measure(prec, 1)
+        compare[prec] = dict(summary(*runs2[0]), saturation_pairs_per_s=sat2["pairs_per_s"],
+                             saturation_mean_batch=sat2["mean_batch"], arrival_rate_per_s=rate2)
     mp_per_pair = sum(W * H for _, W, H, _, _ in streams) / len(streams) / 1e6
-    others = {}
-    for frac in [float(x) for x in args.extra_loads.split(",") if x.strip()]:
-        r2 = sv.Scheduler(ex, max_batch=64, slots=4, hbm_budget=40e9).run(
-            requests(args.requests, frac * sat["pairs_per_s"], 3))
-        others[str(frac)] = {"arrival_rate_per_s": frac * sat["pairs_per_s"], "pairs_per_s": r2["pairs_per_s"],
-                             "p50_ms": r2["p50_ms"], "p99_ms": r2["p99_ms"], "mean_batch": r2["mean_batch"]}
-    ex.close()
     line = {"mode": "serve", "metric": "streaming mix p50/p99 latency and pairs/s", "unit": "pairs/s",
             "value": rep["pairs_per_s"], "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "max_ms": rep["max_ms"],
             "requests": rep["requests"], "dropped": rep["dropped"], "mean_batch": rep["mean_batch"],
+            "host_busy_frac": rep["host_busy_frac"], "host_us_per_batch": rep["host_us_per_batch"],
             "arrival_rate_per_s": rate, "saturation_pairs_per_s": sat["pairs_per_s"],
-            "saturation_mean_batch": sat["mean_batch"], "mean_megapixels_per_pair": mp_per_pair,
+            "saturation_mean_batch": sat["mean_batch"], "saturation_host_busy_frac": sat["host_busy_frac"],
+            "mean_megapixels_per_pair": mp_per_pair,
+            "p99_ms_per_run": p99s, "p99_spread": max(p99s) / max(1e-9, min(p99s)),
+            "runs": [summary(*r) for r in runs],
             "latency_by_frame_size": per_size, "latency_split": split, "steady_state": steady_p,
-            "other_loads": others,
-            "config": {"streams": args.streams, "sizes": wl.SERVING_SIZES, "precision": "bf16", "slots": 4,
-                       "max_pairs_per_launch": 64, "max_megapixels_per_launch": 16, "hbm_budget_gb": 40,
-                       "ring_frames_per_stream": ring, "graphs_prewarmed": True},
+            "other_loads": others, "other_precisions": compare,
+            "config": {"streams": args.streams, "sizes": wl.SERVING_SIZES, "precision": args.serve_precision,
+                       "slots": slots, "max_pairs_per_launch": 64, "max_megapixels_per_launch": 16,
+                       "hbm_budget_gb": 40, "ring_frames_per_stream": ring, "graphs_prewarmed": True,
+                       "repeats": len(runs)},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
@@ -363,8 +403,38 @@ def run_preprocess(args):
     torch.cuda.synchronize()
     path_ms = e0.elapsed_time(e1) / 20
     eng.close()
+    # temporal smoothing of a field of 64 Mi floats (> L2): x and the state read, the state written
+    n_ema = 1 << 26
+    x = torch.rand(n_ema, device="cuda")
+    st = torch.rand(n_ema, device="cuda")
+    for _ in range(3):
+        rp.stage_ema(x, st, 0.5)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        rp.stage_ema(x, st, 0.5)
+    e1.record()
+    torch.cuda.synchronize()
+    ema_ms = e0.elapsed_time(e1) / 20
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    pre_b = 2 * W * H * (2 + 4)  # both frames: u16 in, float out
+    ema_b = 12 * n_ema
     print(json.dumps({"mode": "preprocess", "workload": WORKLOAD, "preprocess_ms_per_pair": pre_ms,
-                      "path_ms_per_pair_float_frames": path_ms, "data": "synthetic"}), flush=True)
+                      "path_ms_per_pair_float_frames": path_ms, "ema_ms_64mi": ema_ms,
+                      "roofline": {"peak_gbs": hbm,
+                                   "preprocess": {"algorithmic_bytes": pre_b, "gbs": pre_b / (pre_ms * 1e-3) / 1e9,
+                                                  "frac": pre_b / (pre_ms * 1e-3) / 1e9 / hbm,
+                                                  "what": "u16 frames in, float frames out (one pair; launch- and "
+                                                          "latency-bound at this size)"},
+                                   "ema": {"algorithmic_bytes": ema_b, "gbs": ema_b / (ema_ms * 1e-3) / 1e9,
+                                           "frac": ema_b / (ema_ms * 1e-3) / 1e9 / hbm,
+                                           "what": "x and state read, state written, 64 Mi floats"}},
+                      "data": "synthetic"}), flush=True)
     return 0
 
 
@@ -486,9 +556,21 @@ def run_adjoint(args):
     torch.cuda.synchronize()
     ref_ms = 1000 * (time.perf_counter() - t0)
     e_before = float(np.median(np.hypot(u.cpu().numpy() - tu, v.cpu().numpy() - tv)))
+    # the adjoint must read both frames and the field, and write the gradient
+    alg = 2 * W * H * 1 + 125 * 125 * 4 * 4
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = alg / (ms * 1e-3) / 1e9
     line = {"mode": "adjoint", "workload": "diff_1mp_u8: 1024x1024 u8, 32 px at 75 %, 125x125 nodes",
             "score_and_grad_ms": ms, "refine_5_steps_ms": ref_ms, "score_history": hist,
-            "median_error_px_before": e_before, "data": "synthetic"}
+            "median_error_px_before": e_before,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": alg, "gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                         "what": "frames A, B (u8) and the field read, the gradient written, per call"},
+            "data": "synthetic"}
     eng.close()
     print(json.dumps(line), flush=True)
     return 0
@@ -767,7 +849,7 @@ def main():
     outs = [eng.empty_outputs(B) for _ in range(2)]
     host_outs = [[torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs[0]] for _ in range(2)]
     out_bytes = sum(o.numel() * o.element_size() for o in outs[0])
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(30, args.steps)
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream(device=dev)
     uploaded = [torch.cuda.Event() for _ in range(2)]
@@ -873,6 +955,8 @@ def main():
                 "executed_frac": plane_flops / (per_launch_ms / 1000.0) / 1e12 / peak,
                 "fp32_fma_peak": fma, "fp32_derived_peak_tflops": fp32_derived}
     stage_ms = {r["name"]: r["total_ms"] / r["launches"] for r in recs}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kernels = kernel_roofline(recs, 2, 8, hbm_peak)  # u16 frames, margin 8 (radius 4)
     launches_per_step = sum(r["launches"] for r in recs) / 3.0
 
     # ---- CPU baseline and accuracy against the FP64 oracle
@@ -907,12 +991,54 @@ def main():
             "paths": paths, "latency": latency, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": int(round(launches_per_step * args.steps)),
             "stage_ms_per_launch": stage_ms,
+            "kernel_roofline": {"peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs", "rows": kernels},
             "vectors_per_s": value * 127 * 127,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def kernel_bytes(rec: dict, bpp: int, margin: int) -> int | None:
+    """Algorithmic DRAM bytes of one traced launch (the data the step must
+    move, independent of how the kernel schedules it): frames read once and
+    written once, node fields read and written once.  rec: a stage-trace record
+    (name, pairs, image size, grid)."""
+    name, n, W, H = rec["name"], rec["pairs"], rec["width"], rec["height"]
+    nodes = rec["nx"] * rec["ny"]
+    if name == "ingest":  # u8/u16 frame in, float frame (interior) out
+        return n * W * H * (bpp + 4)
+    if name.startswith("down/"):  # a frame in (the input format at level 1, float above), its half out
+        src = bpp if name == "down/L1" else 4
+        return n * (W * H * src + (W // 2) * (H // 2) * 4)
+    if name.startswith("deform"):  # frame in, warped float frame with margins out
+        src = 4 if "/L" in name else bpp
+        return n * (W * H * src + (W + 2 * margin) * (H + 2 * margin) * 4)
+    if name.startswith("uod/"):  # u, v, info in; u, v, mask out
+        return n * nodes * 21
+    if name.startswith("interp/"):  # u, v out (and the coarser field in)
+        return n * nodes * 16
+    if name == "vort":  # u, v in; vorticity out
+        return n * nodes * 12
+    if name.startswith("pass/"):  # frames A and B' read (the pass is bound by the ALU)
+        return n * W * H * 4 * 2
+    return None
+
+
+def kernel_roofline(recs: list, bpp: int, margin: int, hbm_gbs: float) -> list:
+    """Achieved bandwidth of every traced kernel against the measured HBM peak."""
+    rows = []
+    for r in recs:
+        b = kernel_bytes(r, bpp, margin)
+        ms = r["total_ms"] / r["launches"]
+        if b is None or ms <= 0:
+            continue
+        gbs = b / (ms * 1e-3) / 1e9
+        rows.append({"kernel": r["name"], "ms_per_launch": round(ms, 4), "bytes_per_launch": b,
+                     "gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_gbs, 3),
+                     "bound": "alu" if r["name"].startswith("pass/") else "hbm"})
+    return rows
 
 
 def stored_traffic(workload: str, head: str, dom: dict, path: str | None = None):

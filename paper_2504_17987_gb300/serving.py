@@ -136,6 +136,7 @@ class Scheduler:
         self.dropped: List[Request] = []
         self.t0 = 0.0
         self.batches = 0
+        self.host_busy = 0.0           # seconds of loop iterations that completed or started work
 
     # ---------------------------------------------------------- accounting --
     def _engine_charge(self, key: Key, mode: str, slot: int) -> int:
@@ -270,9 +271,12 @@ class Scheduler:
                         self.dropped.append(r)
                     else:
                         self.fifo[r.stream].append(r)
+                t_it = self.clock()
                 progressed = self._complete(now_fn)
                 progressed |= self._dispatch(now_fn())
-                if not progressed:
+                if progressed:
+                    self.host_busy += self.clock() - t_it
+                else:
                     if pause_gc and gc.get_count()[0] >= young_gc_at:
                         gc.collect(1)
                     if on_idle is not None:
@@ -294,18 +298,20 @@ class Scheduler:
         return {"requests": len(self.done), "dropped": len(self.dropped), "wall_s": wall,
                 "pairs_per_s": len(self.done) / wall if wall > 0 else math.nan,
                 "p50_ms": 1000 * pct(50), "p99_ms": 1000 * pct(99), "max_ms": 1000 * (lat[-1] if lat else math.nan),
-                "batches": self.batches, "mean_batch": len(self.done) / max(1, self.batches)}
+                "batches": self.batches, "mean_batch": len(self.done) / max(1, self.batches),
+                "host_busy_frac": self.host_busy / wall if wall > 0 else math.nan,
+                "host_us_per_batch": 1e6 * self.host_busy / max(1, self.batches)}
 
 
 # ------------------------------------------------------------- GPU executor --
 
-def warm_config(W: int, H: int, bits: int, precision: str = "bf16", max_batch: int = 64):
+def warm_config(W: int, H: int, bits: int, precision: str = "fp32", max_batch: int = 64):
     from .binding import Config
     return Config(W, H, windows=(16,), overlaps=(0.5,), radii=(4,), levels=0, bit_depth=bits,
                   precision=precision, max_batch=max_batch)
 
 
-def cold_config(W: int, H: int, bits: int, precision: str = "bf16", max_batch: int = 64):
+def cold_config(W: int, H: int, bits: int, precision: str = "fp32", max_batch: int = 64):
     from .binding import Config
     return Config(W, H, windows=(32, 16), overlaps=(0.5, 0.5), radii=(4, 4), levels=2, bit_depth=bits,
                   precision=precision, max_batch=max_batch)
@@ -315,7 +321,7 @@ class GpuExecutor(Executor):
     """Runs batches with librpiv; one engine per (key, mode, slot) and one
     CUDA stream per slot, so batches in different slots overlap."""
 
-    def __init__(self, slots: int, precision: str = "bf16", max_batch: int = 64, cold_batch: int = 8,
+    def __init__(self, slots: int, precision: str = "fp32", max_batch: int = 64, cold_batch: int = 8,
                  device: int = 0, max_megapixels: float = 16.0, prewarm: bool = False, alpha1=None, alpha2=None):
         import torch
         self.torch = torch

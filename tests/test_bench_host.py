@@ -103,3 +103,19 @@ def test_committed_traffic_entries_name_their_geometry():
         workload, head, _, name = key.split("/")
         assert workload in ("paper_1mp", "paper_1mp_r1") and head in ("fp32", "bf16", "fp16")
         assert {"window", "step", "radius", "bytes_per_pair", "source_hash"} <= set(ent)
+
+
+def test_kernel_bytes_count_each_frame_and_field_once():
+    import bench
+    rec = dict(pairs=64, width=1024, height=1024, nx=127, ny=127, launches=3, total_ms=3.0)
+    b = lambda name, **k: bench.kernel_bytes({**rec, "name": name, **k}, 2, 8)  # noqa: E731
+    assert b("ingest") == 64 * 1024 * 1024 * 6
+    assert b("down/L1") == 64 * (1024 * 1024 * 2 + 512 * 512 * 4)
+    assert b("down/L2", width=512, height=512) == 64 * (512 * 512 * 4 + 256 * 256 * 4)
+    assert b("deform/p2") == 64 * (1024 * 1024 * 2 + 1040 * 1040 * 4)
+    assert b("deform/L1", width=512, height=512) == 64 * (512 * 512 * 4 + 528 * 528 * 4)
+    assert b("uod/p2") == 64 * 127 * 127 * 21 and b("vort") == 64 * 127 * 127 * 12
+    assert b("interp/p1") == 64 * 127 * 127 * 16
+    assert b("pass/p2") == 64 * 1024 * 1024 * 8
+    rows = bench.kernel_roofline([{**rec, "name": "vort"}], 2, 8, 6789.0)
+    assert rows[0]["ms_per_launch"] == 1.0 and abs(rows[0]["gbs"] - 64 * 127 * 127 * 12 / 1e-3 / 1e9) < 0.1
