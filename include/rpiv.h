@@ -263,8 +263,8 @@ rpiv_status rpiv_stage_status(void *cuda_stream, int timeout_ms);
  * about 2000 x 2000 pixels) are rejected with
  * RPIV_ERR_INVALID_ARG.  Every call looks up the array's device address
  * (cudaGetSymbolAddress, which allocates nothing once the library's module is
- * loaded on the device); the first call on a device loads it, so make that
- * first call before any stream capture.  All calls
+ * loaded on the device); the first call on a device loads it, and that is
+ * when the array's memory is taken.  All calls
  * share the one array, so calls whose work overlaps on the GPU (different
  * streams, or other devices' calls are fine) race and must be serialised by
  * the caller; a later call on the same stream is ordered after the earlier.

@@ -954,7 +954,7 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
         return fail(RPIV_ERR_INVALID_ARG, "pitch_bytes smaller than width * bytes per pixel or misaligned");
     DeviceGuard dg(h->device);
     const StageDef &d = h->stages[h->cfg.predictor_levels];  // first full-resolution pass grid
-    const size_t need = adjoint_workspace_bytes(d.W, d.H, d.nx, d.ny);
+    const size_t need = adjoint_workspace_bytes(d.W, d.H, d.w, d.s, d.nx, d.ny);
     if (h->adj_bytes < need) {
         // allocated on first use (not inside a stream capture)
         if (h->adj_ws) {
@@ -987,8 +987,7 @@ rpiv_status rpiv_backward(rpiv_handle *h, const void *img_a, const void *img_b, 
     a.ny = d.ny;
     a.u = u;
     a.v = v;
-    a.win_stats = reinterpret_cast<float *>(h->adj_ws);
-    a.pix_g = a.win_stats + up(8ull * d.nx * d.ny, 64);
+    a.ws = h->adj_ws;
     a.grad_scale = grad_score;
     a.grad_u = grad_u;
     a.grad_v = grad_v;

@@ -254,13 +254,11 @@ struct AdjArgs {
     PtrRef img_a, img_b;
     int w, s, nx, ny;
     const float *u, *v;    // field on the grid
-    float *win_stats;      // workspace: 8 floats per window
-    float *pix_g;          // workspace: 2 floats per pixel (dS/dX, dS/dY at the pixel)
-    float *score_part;     // workspace: one float per window row
+    void *ws;              // workspace of adjoint_workspace_bytes, 256-byte aligned
     float grad_scale;
     float *grad_u, *grad_v, *score_out;
 };
-size_t adjoint_workspace_bytes(int W, int H, int nx, int ny);
+size_t adjoint_workspace_bytes(int W, int H, int w, int s, int nx, int ny);
 cudaError_t launch_adjoint(const AdjArgs &a, cudaStream_t st);
 // Refinement step helpers: cu = u + eta gu (and v), and max(|a|, |b|) into *out.
 cudaError_t launch_refine_axpy(const float *u, const float *v, const float *gu, const float *gv, float eta, float *cu,
