@@ -404,18 +404,33 @@ def stage_vorticity(u, v, s: int, stream=None):
     return o
 
 
-def stage_preprocess(img, vmax: int, hp: int = 7, tiles=(8, 8), clip_pct: int = 200, stream=None):
+def stage_preprocess(img, vmax: int, hp: int = 7, tiles=(8, 8), clip_pct: int = 200, stream=None, out=None,
+                     scratch=None):
     """High-pass filter and CLAHE (Sec. 2) of a u8/u16 device image; returns a
-    float32 image in [0, vmax] (rpiv_stage_preprocess)."""
+    float32 image in [0, vmax] (rpiv_stage_preprocess).  out (H x W float32)
+    and scratch (uint8, at least preprocess_scratch_bytes) may be supplied for
+    reuse."""
     H, W = img.shape
-    nbytes = ctypes.c_size_t()
-    _check(load().rpiv_stage_preprocess_scratch_bytes(W, H, int(tiles[0]), int(tiles[1]), ctypes.byref(nbytes)))
-    scratch = _fresh(torch.empty(nbytes.value, dtype=torch.uint8, device=img.device))
-    out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    nbytes = preprocess_scratch_bytes(W, H, tiles)
+    if scratch is None:
+        scratch = _fresh(torch.empty(nbytes, dtype=torch.uint8, device=img.device))
+    elif scratch.dtype != torch.uint8 or scratch.numel() < nbytes or not scratch.is_contiguous():
+        raise ValueError(f"scratch: a contiguous uint8 tensor of at least {nbytes} bytes")
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    elif out.dtype != torch.float32 or tuple(out.shape) != (H, W) or not out.is_contiguous():
+        raise ValueError("out: a contiguous float32 tensor of the image's shape")
     _check(load().rpiv_stage_preprocess(_ptr(img), img.stride(0) * img.element_size(), _fmt_code(img), W, H,
                                         int(vmax), int(hp), int(tiles[0]), int(tiles[1]), int(clip_pct), _ptr(out),
-                                        _ptr(scratch), nbytes.value, _stream(stream)))
+                                        _ptr(scratch), scratch.numel(), _stream(stream)))
     return out
+
+
+def preprocess_scratch_bytes(W: int, H: int, tiles=(8, 8)) -> int:
+    """Scratch bytes rpiv_stage_preprocess needs for a W x H image."""
+    nbytes = ctypes.c_size_t()
+    _check(load().rpiv_stage_preprocess_scratch_bytes(W, H, int(tiles[0]), int(tiles[1]), ctypes.byref(nbytes)))
+    return nbytes.value
 
 
 def stage_ema(x, state, alpha: float, init: bool = False, stream=None):

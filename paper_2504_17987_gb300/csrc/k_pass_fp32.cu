@@ -1,7 +1,71 @@
-// FP32 CUDA-core instantiations of the fused correlation pass.
+// FP32 CUDA-core instantiations of the fused correlation pass, and the
+// tensor maps every pass kernel loads its regions through.
+#include <cudaTypedefs.h>
+
 #include "pass_impl.cuh"
 
 namespace rpiv {
+
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against the driver library); null where it is unavailable
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// A float frame of the margin layout per pair: columns (pitch), rows, pairs.
+bool encode_frames(CUtensorMap *m, const char *base, long long pitch, long long rows, int pairs,
+                   long long pair_stride, int box_w, int box_h)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn || !base || pitch <= 0 || rows <= 0 || pairs < 1) return false;
+    const long long row_bytes = pitch * 4;
+    if (pairs == 1) pair_stride = row_bytes * rows;
+    if (((uintptr_t)base & 15) || (row_bytes & 15) || pair_stride <= 0 || (pair_stride & 15)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)pairs};
+    const cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)pair_stride};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<char *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// The regions of a tile are a_pitch x ah floats of frame A (or the warped A')
+// and b_pitch x BR floats of B', at column offsets that are multiples of 4
+// (steps that are multiples of 4): one box each per load instead of one bulk
+// copy per row.  Boxes reach a few columns past a region (the row pitch of
+// the shared-memory copy) and, at the last tiles, past the frame, which the
+// copy fills with zeros; the kernels read only the region.
+void attach_region_maps(PassArgs &a, int n_pairs)
+{
+    a.tma = 0;
+    const PassPlan &P = a.plan;
+    if (!P.tma_ok || n_pairs < 1 || a.s % 4 != 0) return;
+    const PtrRef &ar = a.adef.base ? a.adef : a.afl;
+    const PtrRef &br = a.bdef;
+    if (!ar.base || !br.base || ar.indirect || br.indirect) return;
+    if (n_pairs > 1 && (ar.stride <= 0 || br.stride <= 0)) return;
+    const long long rows = (long long)a.H + 2LL * a.def_margin;
+    if (!encode_frames(&a.tm_a, ar.base, a.def_pitch, rows, n_pairs, ar.stride, P.a_pitch, P.box_ah)) return;
+    if (!encode_frames(&a.tm_b, br.base, a.def_pitch, rows, n_pairs, br.stride, P.b_pitch, P.box_br)) return;
+    a.tma = 1;
+}
 
 template <int RC, int GC = 0>
 static cudaError_t go_fp32(const PassArgs &a, dim3 grid, int smem, cudaStream_t st)

@@ -66,40 +66,58 @@ __device__ __forceinline__ int bin_of(int d, long long den)
     return b > NBINS - 1 ? NBINS - 1 : (int)b;
 }
 
-// One CTA per tile: histogram, clip, spread, cumulative map.
-__global__ void __launch_bounds__(NBINS) clahe_maps(const PreArgs a, const int *D, float *maps)
+// One CTA of MAP_THREADS per tile: histogram, clip, spread, cumulative map.
+// Background-dominated particle images put most pixels of a tile in a few
+// bins, so lanes of a warp that hold the same bin add their count with one
+// shared-memory atomic (the lane with the lowest index of the group).  The
+// cumulative counts are an exact integer scan over the 256 bins (warp scans,
+// then the warps' totals); each bin's map value is then formed on its own.
+constexpr int MAP_THREADS = 1024;
+
+__global__ void __launch_bounds__(MAP_THREADS) clahe_maps(const PreArgs a, const int *D, float *maps)
 {
     __shared__ int h[NBINS];
     __shared__ int excess;
-    const int ti = blockIdx.x, tj = blockIdx.y, tid = threadIdx.x;
+    __shared__ int wtot[NBINS / 32];
+    const int ti = blockIdx.x, tj = blockIdx.y, tid = threadIdx.x, lane = tid & 31;
     const int tw = (a.W + a.tx - 1) / a.tx, th = (a.H + a.ty - 1) / a.ty;
     const int x0 = ti * tw, x1 = min(a.W, x0 + tw), y0 = tj * th, y1 = min(a.H, y0 + th);
     const long long den = (long long)a.n * (a.vmax + 1);
-    h[tid] = 0;
+    if (tid < NBINS) h[tid] = 0;
     if (tid == 0) excess = 0;
     __syncthreads();
     const int cw = max(x1 - x0, 0), N = cw * max(y1 - y0, 0);
-    for (int e = tid; e < N; e += blockDim.x) {
-        const int y = y0 + e / cw, x = x0 + e % cw;
-        atomicAdd(&h[bin_of(D[(long long)y * a.W + x], den)], 1);
+    // warp-uniform trip count, so that every lane takes part in the match
+    for (int base = tid - lane; base < N; base += blockDim.x) {
+        const int e = base + lane;
+        const int bin = e < N ? bin_of(D[(long long)(y0 + e / cw) * a.W + x0 + e % cw], den) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(grp) - 1) atomicAdd(&h[bin], __popc(grp));
     }
     __syncthreads();
     int L = (int)((long long)a.clip_pct * N / (100LL * NBINS));
     if (L < 1) L = 1;
-    const int over = h[tid] > L ? h[tid] - L : 0;
-    if (over) atomicAdd(&excess, over);
+    if (tid < NBINS) {
+        const int over = h[tid] > L ? h[tid] - L : 0;
+        if (over) atomicAdd(&excess, over);
+    }
     __syncthreads();
-    const int E = excess;
-    h[tid] = min(h[tid], L) + E / NBINS + (tid < E % NBINS ? 1 : 0);
-    __syncthreads();
-    if (tid == 0) {
-        // cumulative counts (256 integers, in order)
-        int c = 0;
-        float *m = maps + ((long long)tj * a.tx + ti) * NBINS;
-        for (int b = 0; b < NBINS; ++b) {
-            c += h[b];
-            m[b] = N > 0 ? (float)((double)c * a.vmax / (double)N) : 0.f;
+    int c = 0;
+    if (tid < NBINS) {
+        const int E = excess;
+        c = min(h[tid], L) + E / NBINS + (tid < E % NBINS ? 1 : 0);
+        // inclusive scan within the warp, then the totals of the warps before
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += t;
         }
+        if (lane == 31) wtot[tid >> 5] = c;
+    }
+    __syncthreads();
+    if (tid < NBINS) {
+        for (int k = 0; k < (tid >> 5); ++k) c += wtot[k];
+        float *m = maps + ((long long)tj * a.tx + ti) * NBINS;
+        m[tid] = N > 0 ? (float)((double)c * a.vmax / (double)N) : 0.f;
     }
 }
 
@@ -171,7 +189,7 @@ cudaError_t launch_preprocess(const PreArgs &a, void *scratch, cudaStream_t st)
     }
     if (a.fmt == PIX_U8) hp_cols<uint8_t><<<grid, 256, 0, st>>>(a, R, D);
     else hp_cols<uint16_t><<<grid, 256, 0, st>>>(a, R, D);
-    if (a.clip_pct > 0) clahe_maps<<<dim3(a.tx, a.ty), NBINS, 0, st>>>(a, D, maps);
+    if (a.clip_pct > 0) clahe_maps<<<dim3(a.tx, a.ty), MAP_THREADS, 0, st>>>(a, D, maps);
     clahe_apply<<<grid, 256, 0, st>>>(a, D, maps, a.out);
     return cudaGetLastError();
 }

@@ -124,6 +124,25 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
 // completes, so the wait costs few issue slots
 constexpr uint32_t MBAR_SUSPEND_NS = 256;
 
+// One box of a 3-D tensor map (column, row, pair) into shared memory,
+// completing on the barrier; x is a multiple of 4 floats (16 bytes), y and z
+// are in range, and the box's parts past the frame read as zeros.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// The regions as two tensor-map boxes (one instruction each) when the launch
+// attached the maps and both destinations sit on 128-byte boundaries.
+__device__ __forceinline__ bool regions_by_tma(const PassArgs &a, const float *As, const float *Bs)
+{
+    return a.tma && ((smem_addr(As) | smem_addr(Bs)) & 127u) == 0;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -157,7 +176,9 @@ static __device__ __forceinline__ bool load_regions(const PassArgs &a, const Til
         // B' rows start at smem column 0, i.e. global column ax0 + M - padl
         const float *b0 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 + M - P.padl);
         const int acols = up4(g.aw), bcols = up4(g.OFFB + g.BC);
-        const uint32_t bytes = (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
+        const bool tma = regions_by_tma(a, As, Bs);
+        const uint32_t bytes = tma ? (uint32_t)(P.box_ah * P.a_pitch + P.box_br * P.b_pitch) * 4u
+                                   : (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
         // warp 0 alone issues the copies and polls the barrier; the other
         // warps wait at the caller's CTA barrier, which also makes the staged
         // rows visible to them, and leave the issue slots to co-resident CTAs
@@ -171,8 +192,15 @@ static __device__ __forceinline__ bool load_regions(const PassArgs &a, const Til
         __syncwarp();
         if (lane == 0) mbar_expect_tx(bar, bytes);
         __syncwarp();
-        for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
-        for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
+        if (tma) {
+            if (lane == 0) {
+                tma_load_3d(As, &a.tm_a, g.ax0 + M, g.ay0 + M, pair, bar);
+                tma_load_3d(Bs, &a.tm_b, g.ax0 + M - P.padl, g.ay0 - (g.R + 1) + M, pair, bar);
+            }
+        } else {
+            for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
+            for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
+        }
         uint32_t parity = (uint32_t)step & 1u;
         const int lim = a.spin > 0 ? a.spin : MBAR_SPIN_LIMIT;
         bool landed = false;
@@ -239,7 +267,9 @@ static __device__ __forceinline__ void issue_regions(const PassArgs &a, const Ti
     const float *a0 = asrc + (long long)(g.ay0 + M) * dp + (g.ax0 + M);
     const float *b0 = bsrc + (long long)(g.ay0 - (g.R + 1) + M) * dp + (g.ax0 + M - P.padl);
     const int acols = up4(g.aw), bcols = up4(g.OFFB + g.BC);
-    const uint32_t bytes = (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
+    const bool tma = regions_by_tma(a, As, Bs);
+    const uint32_t bytes = tma ? (uint32_t)(P.box_ah * P.a_pitch + P.box_br * P.b_pitch) * 4u
+                               : (uint32_t)(g.ah * acols + g.BR * bcols) * 4u;
     if (lane == 0) {
         if (step == 0) mbar_init(bar, 1);
         fence_proxy_async();
@@ -247,6 +277,13 @@ static __device__ __forceinline__ void issue_regions(const PassArgs &a, const Ti
     __syncwarp();
     if (lane == 0) mbar_expect_tx(bar, bytes);
     __syncwarp();
+    if (tma) {
+        if (lane == 0) {
+            tma_load_3d(As, &a.tm_a, g.ax0 + M, g.ay0 + M, pair, bar);
+            tma_load_3d(Bs, &a.tm_b, g.ax0 + M - P.padl, g.ay0 - (g.R + 1) + M, pair, bar);
+        }
+        return;
+    }
     for (int r = lane; r < g.ah; r += 32) bulk_copy(As + r * P.a_pitch, a0 + (long long)r * dp, acols * 4, bar);
     for (int r = lane; r < g.BR; r += 32) bulk_copy(Bs + r * P.b_pitch, b0 + (long long)r * dp, bcols * 4, bar);
 }
@@ -1209,7 +1246,7 @@ static __device__ __forceinline__ void invalid_tile(const PassArgs &a, const Til
 template <int RC, int PREC, int GC>
 __global__ void __launch_bounds__(PASS_THREADS,
                                   (PREC == PREC_FP32 && (RC >= 0 && RC <= 4) && GC != 32 && !(GC == 8 && RC == 4)) ? 5 : 3)
-    pass_kernel(const PassArgs a)
+    pass_kernel(const __grid_constant__ PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const PassPlan &P = a.plan;
@@ -1329,7 +1366,7 @@ __global__ void __launch_bounds__(PASS_THREADS,
 // direct stencil), so that they overlap the fit.  GC is a multiple of 4: every
 // region row is one bulk copy.
 template <int RC, int GC>
-__global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(const PassArgs a)
+__global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(const __grid_constant__ PassArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const PassPlan &P = a.plan;

@@ -162,8 +162,13 @@ Layout layout_for(int TX, int TY, int w, int s, int R, int G, int prec, bool str
         off = up(off + bytes, 16);
         return o;
     };
+    // the regions start on 128-byte boundaries (tensor-map destinations)
     p.off_a = take(ah * p.a_pitch * 4);
+    off = up(off, 128);
     p.off_b = take(BR * p.b_pitch * 4);
+    p.box_ah = ah;
+    p.box_br = BR;
+    p.tma_ok = (s % 4 == 0 && p.a_pitch <= 256 && p.b_pitch <= 256 && ah <= 256 && BR <= 256) ? 1 : 0;
     p.off_v = take(2 * vh * p.v_pitch * 4);
     p.off_stats = take(2 * nwin * 4);
     p.off_red = take(16);      // the region loads' mbarrier
@@ -301,9 +306,10 @@ Layout layout_for_tc(int TX, int TY, int w, int s, int R, int ns)
 
 // RPIV_TC_PLANES=1 runs the tcgen05 kernel for the shapes it covers (tests
 // run both kernels); read at each plan.  The mma.sync kernel is the default:
-// measured on GB300 at 1 MP it is faster (6.5k against 4.1k pairs/s), since a
-// tcgen05.mma of K = 16 takes about 146 cycles whatever its N, and the banded
-// correlation fills at most 16 of its columns usefully.
+// measured on GB300 at 1 MP it is faster (6.3k against 4.1k pairs/s).  One
+// thread's tcgen05.mma of K = 16 complete about 150 cycles apart whatever N
+// is; the banded correlation fills at most 16 N columns of an MMA usefully,
+// and the kernel has one issuing thread per CTA.
 bool tc_planes_enabled()
 {
     const char *e = std::getenv("RPIV_TC_PLANES");
@@ -516,7 +522,8 @@ cudaError_t launch_pass(const PassArgs &args_in, int n_pairs, cudaStream_t st)
             }
         }
     }
-    const PassArgs &args = *pa;
+    PassArgs args = *pa;
+    attach_region_maps(args, n_pairs);
     dim3 grid(args.plan.tiles_x, args.plan.tiles_y, n_pairs);
     const int smem = args.plan.smem_bytes;
     switch (args.prec) {

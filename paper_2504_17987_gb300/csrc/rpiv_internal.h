@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace rpiv {
@@ -96,6 +97,9 @@ struct PassPlan {
     int cp_group;  // bytes per group slot of the ring
     int off_ebuf, tmem_cols;
     int off_refit;  // FP32 block planes of the refit, |s| <= 2 (25 floats per block)
+    // the A and B' regions of a full tile as two tensor-map boxes (a_pitch x ah
+    // and b_pitch x BR floats, each dimension at most 256): 1 when they fit
+    int tma_ok, box_ah, box_br;
 };
 
 struct PassArgs {
@@ -120,7 +124,16 @@ struct PassArgs {
     PassPlan plan;
     PassPlan strip;        // strip alternative to the tile plan (strip_rows 0: none); the
                            // launch takes it when the batch gives it enough CTAs
+    // set at launch (attach_region_maps): 3-D tensor maps (column, row, pair)
+    // of the A and B' float frames whose boxes are the plan's regions; tma = 0:
+    // the regions are loaded row by row
+    int tma;
+    CUtensorMap tm_a, tm_b;
 };
+// Encodes the region tensor maps into a for a launch of n_pairs (frames at a
+// uniform pair stride); leaves a.tma = 0 where the plan's boxes, the frames or
+// the encoder do not allow them.
+void attach_region_maps(PassArgs &a, int n_pairs);
 
 struct DeformArgs {
     PtrRef img;

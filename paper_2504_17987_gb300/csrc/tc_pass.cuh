@@ -535,7 +535,7 @@ static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, cons
 // FP32 statistics and box sums as in pass_kernel, the FP32 refit planes, the
 // tensor-core phase, argmax on the planes, the refit, the Gaussian fit.
 template <int PREC, int GC>
-__global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const PassArgs a)
+__global__ void __launch_bounds__(PASS_THREADS, 2) tc_pass_kernel(const __grid_constant__ PassArgs a)
 {
     constexpr int R = TC_R;
     extern __shared__ __align__(16) unsigned char smem[];

@@ -18,6 +18,7 @@ cudaError_t prepare_pass_fp16() { return cudaErrorNotSupported; }
 cudaError_t prepare_pass_fp32() { return cudaErrorNotSupported; }
 bool pass_supported_bf16(int R) { return R >= 0 && R <= 16; }
 bool pass_supported_fp16(int R) { return R >= 0 && R <= 16; }
+void attach_region_maps(PassArgs &a, int) { a.tma = 0; }
 }  // namespace rpiv
 
 extern "C" cudaError_t cudaGetDevice(int *d)
