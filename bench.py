@@ -63,8 +63,11 @@ def parse():
     p.add_argument("--serve-precision", default="fp32", choices=["fp32", "bf16", "fp16"],
                    help="correlation precision of the serving mix")
     p.add_argument("--serve-compare", default="", help="further precisions measured in the serving mix, e.g. bf16")
-    p.add_argument("--slots", type=int, default=4, help="concurrent batches (CUDA streams) in the serving mix")
+    p.add_argument("--slots", type=int, default=8, help="concurrent batches (CUDA streams) in the serving mix")
     p.add_argument("--repeats", type=int, default=3, help="Poisson runs at --load with fresh arrival seeds")
+    p.add_argument("--upload", default="engine", choices=["engine", "executor"],
+                   help="serve mode: pinned host frames read by the engine's upload kernel, or copied to the "
+                        "device by the executor (one copy call per image)")
     return p.parse_args()
 
 
@@ -195,7 +198,8 @@ def run_serve(args):
                 "host_busy_frac": rep["host_busy_frac"], "host_us_per_batch": rep["host_us_per_batch"]}
 
     def measure(precision, repeats):
-        ex = sv.GpuExecutor(slots=slots, precision=precision, max_batch=64, cold_batch=8, prewarm=True)
+        ex = sv.GpuExecutor(slots=slots, precision=precision, max_batch=64, cold_batch=8, prewarm=True,
+                            host_frames=args.upload == "engine")
         # every engine (frame size, mode, slot) and every batch size's graph exist before any timing
         for key in sorted({(W, H, bits) for _, W, H, bits, _ in streams}):
             for mode in (sv.COLD, sv.WARM):
@@ -256,7 +260,7 @@ def run_serve(args):
             "config": {"streams": args.streams, "sizes": wl.SERVING_SIZES, "precision": args.serve_precision,
                        "slots": slots, "max_pairs_per_launch": 64, "max_megapixels_per_launch": 16,
                        "hbm_budget_gb": 40, "ring_frames_per_stream": ring, "graphs_prewarmed": True,
-                       "repeats": len(runs)},
+                       "repeats": len(runs), "upload": args.upload},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0

@@ -90,6 +90,13 @@ typedef struct {
     rpiv_precision precision;   /* correlation-plane arithmetic                    */
     rpiv_deform deform_mode;    /* RPIV_DEFORM_B (default) or RPIV_DEFORM_CENTRAL   */
     int max_batch;              /* 1..RPIV_MAX_BATCH pairs per rpiv_process_batch   */
+    int host_frames;            /* 0: img_a / img_b of rpiv_process_batch and
+                                   rpiv_process_pair are device memory; 1: they are
+                                   page-locked host memory (cudaHostAlloc,
+                                   cudaMallocHost), which every launch sequence
+                                   reads once into the handle's workspace with one
+                                   upload kernel (part of the captured graph), so
+                                   that no copy call is made per image           */
 } rpiv_config;
 
 typedef struct rpiv_handle rpiv_handle;
@@ -138,6 +145,8 @@ rpiv_status rpiv_process_pair(rpiv_handle *h, const void *img_a, const void *img
  * has a predictor) or hold NULL entries (that pair uses the pyramid), vort
  * and mask may be NULL or hold NULL entries.  Launch sequences are captured
  * once per (n, predictor pattern) as a CUDA graph and replayed.
+ * With cfg.host_frames = 1 the image pointers are page-locked host memory,
+ * read by the device (checked per call: RPIV_ERR_INVALID_ARG otherwise).
  * Errors: INVALID_ARG (n outside [1, max_batch], nulls), CUDA.               */
 rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, const void *const *img_b,
                                size_t pitch_bytes, const float *const *pred_u, const float *const *pred_v,

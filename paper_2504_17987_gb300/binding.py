@@ -63,6 +63,7 @@ class _Config(ctypes.Structure):
         ("search_radius", ctypes.c_int * 4), ("predictor_levels", ctypes.c_int),
         ("uod_threshold", ctypes.c_float), ("uod_eps", ctypes.c_float), ("replace_outliers", ctypes.c_int),
         ("precision", ctypes.c_int), ("deform_mode", ctypes.c_int), ("max_batch", ctypes.c_int),
+        ("host_frames", ctypes.c_int),
     ]
 
 
@@ -147,6 +148,7 @@ class Config:
     deform: str = "b"
     max_batch: int = 1
     float_frames: bool = False  # frames are float32 (for example pre-processed), not u8/u16
+    host_frames: bool = False   # process_pair/process_batch take page-locked host (pinned CPU) tensors
 
     @property
     def fmt(self) -> int:
@@ -171,6 +173,7 @@ class Config:
         c.precision = PRECISIONS[self.precision]
         c.deform_mode = RPIV_DEFORM_CENTRAL if self.deform == "central" else RPIV_DEFORM_B
         c.max_batch = self.max_batch
+        c.host_frames = 1 if self.host_frames else 0
         return c
 
     @classmethod
@@ -188,8 +191,11 @@ def validate_config(cfg: Config) -> Tuple[int, int]:
     return nx.value, ny.value
 
 
-def _img_check(t: torch.Tensor, cfg_fmt: int):
-    if not t.is_cuda:
+def _img_check(t: torch.Tensor, cfg_fmt: int, host: bool = False):
+    if host:
+        if t.is_cuda or not t.is_pinned():
+            raise ValueError("a host_frames engine takes pinned CPU tensors")
+    elif not t.is_cuda:
         raise ValueError("images must be CUDA tensors")
     if cfg_fmt == RPIV_F32:
         ok = t.dtype == torch.float32
@@ -248,8 +254,8 @@ class Engine:
 
     def process_pair(self, a: torch.Tensor, b: torch.Tensor, pred=None, out=None, stream=None):
         """Returns (u, v, vort, mask) on the final-pass grid (asynchronous)."""
-        _img_check(a, self.cfg.fmt)
-        _img_check(b, self.cfg.fmt)
+        _img_check(a, self.cfg.fmt, self.cfg.host_frames)
+        _img_check(b, self.cfg.fmt, self.cfg.host_frames)
         if a.stride(0) != b.stride(0):
             raise ValueError("A and B must share the row pitch")
         u, v, w, m = out if out is not None else self.empty_outputs(1)
@@ -267,7 +273,7 @@ class Engine:
             raise ValueError("a_list and b_list differ in length")
         pitch = a_list[0].stride(0) * a_list[0].element_size()
         for t in list(a_list) + list(b_list):
-            _img_check(t, self.cfg.fmt)
+            _img_check(t, self.cfg.fmt, self.cfg.host_frames)
             if t.stride(0) * t.element_size() != pitch:
                 raise ValueError("all images of a batch must share the row pitch")
         if outs is None:

@@ -102,6 +102,7 @@ std::string check_config(const rpiv_config *c, std::vector<StageDef> *stages_out
     if (c->n_passes < 1 || c->n_passes > RPIV_MAX_PASSES) return "n_passes must be in [1, 4]";
     if (c->predictor_levels < 0 || c->predictor_levels > RPIV_MAX_LEVELS) return "predictor_levels must be in [0, 4]";
     if (c->max_batch < 1 || c->max_batch > RPIV_MAX_BATCH) return "max_batch must be in [1, 64]";
+    if (c->host_frames != 0 && c->host_frames != 1) return "host_frames must be 0 or 1";
     if (c->precision != RPIV_FP32 && c->precision != RPIV_BF16 && c->precision != RPIV_FP16)
         return "unknown precision";
     if (c->deform_mode != RPIV_DEFORM_B && c->deform_mode != RPIV_DEFORM_CENTRAL) return "unknown deform_mode";
@@ -180,6 +181,8 @@ struct rpiv_handle {
     // frame B at pyramid level l >= 1
     size_t frame_off[RPIV_MAX_LEVELS + 1][2] = {};
     size_t def_off[2] = {};  // per-pair offsets of the warped frames B' (and A')
+    size_t in_off[2] = {};   // host_frames: per-pair offsets of the uploaded frames A and B
+    long long in_pitch = 0;  // host_frames: bytes between their rows (a multiple of 16)
     int margin = 0;          // M of every frame
     size_t pair_stride = 0;
     int *err_dev = nullptr;  // error word of the kernels' bounded waits
@@ -415,13 +418,34 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
     };
     rpiv_status rs;
 
+    // the caller's frames: the pointer table entries, or (host frames) the
+    // workspace copies the upload kernel makes of them first
+    PtrRef img_a = tab(&io[0].a), img_b = tab(&io[0].b);
+    long long img_pitch = (long long)pitch;
+    if (c.host_frames) {
+        UploadArgs ua;
+        ua.src_a = img_a;
+        ua.src_b = img_b;
+        ua.pitch = (long long)pitch;
+        ua.dst_a = ws(h->in_off[0]);
+        ua.dst_b = ws(h->in_off[1]);
+        ua.dst_pitch = h->in_pitch;
+        ua.row_bytes = c.width * (user_fmt == PIX_U8 ? 1 : (user_fmt == PIX_U16 ? 2 : 4));
+        ua.H = c.height;
+        TraceScope ts(h, st, "upload", geom_of(c.width, c.height, 0, 0, 0, 0, 0, n));
+        CK(launch_upload(ua, n, st), "upload launch");
+        img_a = ua.dst_a;
+        img_b = ua.dst_b;
+        img_pitch = h->in_pitch;
+    }
+
     bool pass0_pred = false;
     if (!central) {
         // frame A as float, read by every full-resolution pass
         IngestArgs ia;
-        ia.src = tab(&io[0].a);
+        ia.src = img_a;
         ia.fmt = user_fmt;
-        ia.pitch = (long long)pitch;
+        ia.pitch = img_pitch;
         ia.W = c.width;
         ia.H = c.height;
         ia.dst = ws(h->frame_off[0][0]);
@@ -436,9 +460,9 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
             for (int ab = 0; ab < 2; ++ab) {
                 DownArgs d;
                 if (l == 1) {
-                    d.src = tab(ab ? (const void *)&io[0].b : (const void *)&io[0].a);
+                    d.src = ab ? img_b : img_a;
                     d.fmt = user_fmt;
-                    d.pitch = (long long)pitch;
+                    d.pitch = img_pitch;
                     d.W = c.width;
                     d.H = c.height;
                 } else {
@@ -492,7 +516,7 @@ rpiv_status enqueue_schedule(rpiv_handle *h, int n, size_t pitch, bool any_pred,
             const size_t nprev = (size_t)prev.nx * prev.ny;
             if ((rs = run_interp(prev, ws(prev.off_out), ws(prev.off_out + 4 * nprev), d, 0, 0)) != RPIV_OK) return rs;
         }
-        if ((rs = run_pass(d, tab(&io[0].a), tab(&io[0].b), user_fmt, (long long)pitch, ws(h->frame_off[0][0]),
+        if ((rs = run_pass(d, img_a, img_b, user_fmt, img_pitch, ws(h->frame_off[0][0]),
                            pred)) != RPIV_OK)
             return rs;
         if ((rs = run_uod(d, p == np - 1)) != RPIV_OK) return rs;
@@ -676,6 +700,7 @@ rpiv_status rpiv_config_default(rpiv_config *cfg)
     cfg->precision = RPIV_FP32;
     cfg->deform_mode = RPIV_DEFORM_B;
     cfg->max_batch = 1;
+    cfg->host_frames = 0;
     g_err.clear();
     return RPIV_OK;
 }
@@ -734,6 +759,12 @@ rpiv_status rpiv_create(const rpiv_config *cfg, int device, rpiv_handle **out)
         // the warped frames of the largest stage serve every stage
         h->def_off[1] = take(frame_bytes(cfg->width, cfg->height, M));
         if (central) h->def_off[0] = take(frame_bytes(cfg->width, cfg->height, M));
+        if (cfg->host_frames) {
+            const int bpp = cfg->fmt == RPIV_U8 ? 1 : (cfg->fmt == RPIV_U16 ? 2 : 4);
+            h->in_pitch = (long long)up((size_t)cfg->width * bpp, 16);
+            h->in_off[0] = take((size_t)h->in_pitch * cfg->height);
+            h->in_off[1] = take((size_t)h->in_pitch * cfg->height);
+        }
     }
     for (auto &d : h->stages) {
         const size_t n1 = (size_t)d.nx * d.ny;
@@ -849,6 +880,18 @@ rpiv_status rpiv_process_batch(rpiv_handle *h, int n, const void *const *img_a, 
         else any_nopred = true;
     }
     DeviceGuard dg(h->device);
+    if (h->cfg.host_frames) {
+        // the upload kernel reads the frames through their host addresses
+        for (int i = 0; i < n; ++i)
+            for (const void *p : {img_a[i], img_b[i]}) {
+                cudaPointerAttributes at;
+                if (cudaPointerGetAttributes(&at, p) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+                    cudaGetLastError();
+                    return fail(RPIV_ERR_INVALID_ARG, "host_frames: the image of pair " + std::to_string(i) +
+                                                          " is not page-locked host memory");
+                }
+            }
+    }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // pointer table for this call, staged in a pinned ring slot
     const int slot = h->ring_pos;

@@ -367,6 +367,38 @@ __global__ void ingest_kernel(const IngestArgs a)
     else ingest_row4<float>(row, x, a.W, d, vec);
 }
 
+// One CTA copies UPLOAD_ROWS rows of one frame of one pair: 16-byte words
+// where the source row starts on a 16-byte boundary, bytes otherwise.
+constexpr int UPLOAD_ROWS = 8;
+
+__global__ void __launch_bounds__(256) upload_kernel(const UploadArgs a)
+{
+    const int pair = blockIdx.z, which = blockIdx.y;
+    const unsigned char *src = (const unsigned char *)resolve(which ? a.src_b : a.src_a, pair);
+    unsigned char *dst = (unsigned char *)resolve(which ? a.dst_b : a.dst_a, pair);
+    const int nw = a.row_bytes >> 4;
+    for (int r = 0; r < UPLOAD_ROWS; ++r) {
+        const int y = blockIdx.x * UPLOAD_ROWS + r;
+        if (y >= a.H) return;
+        const unsigned char *s = src + (long long)y * a.pitch;
+        unsigned char *d = dst + (long long)y * a.dst_pitch;
+        if (((uintptr_t)s & 15) == 0) {
+            for (int i = threadIdx.x; i < nw; i += blockDim.x)
+                reinterpret_cast<uint4 *>(d)[i] = reinterpret_cast<const uint4 *>(s)[i];
+            for (int i = (nw << 4) + threadIdx.x; i < a.row_bytes; i += blockDim.x) d[i] = s[i];
+        } else {
+            for (int i = threadIdx.x; i < a.row_bytes; i += blockDim.x) d[i] = s[i];
+        }
+    }
+}
+
+cudaError_t launch_upload(const UploadArgs &a, int n_pairs, cudaStream_t st)
+{
+    dim3 grid((a.H + UPLOAD_ROWS - 1) / UPLOAD_ROWS, 2, n_pairs);
+    upload_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ingest(const IngestArgs &a, int n_pairs, cudaStream_t st)
 {
     dim3 grid((a.W + 4 * 128 - 1) / (4 * 128), a.H, n_pairs);

@@ -866,14 +866,23 @@ __device__ __forceinline__ float log_pos(float c) { return c > 0.f ? logf(c) : 0
 struct WinOut {
     const PassArgs *a;  // the kernel's parameters: pointers are read at the write
     int pair;
-    __device__ __forceinline__ void put(int k, bool ok, int ky, int kx, float dx, float dy) const
+    // the predictor at node k (read early, so that its latency overlaps the fit)
+    __device__ __forceinline__ float2 pred(int k) const
     {
         const float *pu = (const float *)resolve(a->pred_u, pair);
         const float *pv = (const float *)resolve(a->pred_v, pair);
+        return make_float2(pu ? pu[k] : 0.f, pv ? pv[k] : 0.f);
+    }
+    __device__ __forceinline__ void put(int k, bool ok, int ky, int kx, float dx, float dy) const
+    {
+        put(k, ok, ky, kx, dx, dy, pred(k));
+    }
+    __device__ __forceinline__ void put(int k, bool ok, int ky, int kx, float dx, float dy, float2 p) const
+    {
         float *ou = (float *)resolve(a->out_u, pair);
         float *ov = (float *)resolve(a->out_v, pair);
         int32_t *oi = (int32_t *)resolve(a->out_info, pair);
-        const float pu0 = pu ? pu[k] : 0.f, pv0 = pv ? pv[k] : 0.f;
+        const float pu0 = p.x, pv0 = p.y;
         if (!ok) {
             ou[k] = pu0;
             ov[k] = pv0;
@@ -1187,9 +1196,10 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
     for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
         const int wyi = wi / g.nwx, wxi = wi - wyi * g.nwx;
         const int k = (g.wy0 + wyi) * a.nx + (g.wx0 + wxi);
+        const float2 p0 = out.pred(k);
         const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
         if (!(EA > tau)) {
-            out.put(k, false, 0, 0, 0.f, 0.f);
+            out.put(k, false, 0, 0, 0.f, 0.f, p0);
             continue;
         }
         const int q = ws.peaks[wi], need = ws.need[wi];
@@ -1214,7 +1224,7 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
         }
         const float dx = gauss3f(c5[1], c5[0], c5[2], l5[1], l5[0], l5[2]);
         const float dy = gauss3f(c5[3], c5[0], c5[4], l5[3], l5[0], l5[4]);
-        out.put(k, true, ky, kx, dx, dy);
+        out.put(k, true, ky, kx, dx, dy, p0);
     }
 }
 

@@ -258,6 +258,18 @@ struct IngestArgs {
 };
 cudaError_t launch_ingest(const IngestArgs &a, int n_pairs, cudaStream_t st);
 
+// Upload of the caller's host frames (page-locked, device-accessible) into the
+// workspace: per pair, frames A and B of H rows of row_bytes, source rows pitch
+// bytes apart, destination rows dst_pitch bytes apart (a multiple of 16).
+struct UploadArgs {
+    PtrRef src_a, src_b;   // pointer table entries of the frames
+    long long pitch;       // bytes between source rows
+    PtrRef dst_a, dst_b;   // workspace frames
+    long long dst_pitch;   // bytes between destination rows
+    int row_bytes, H;
+};
+cudaError_t launch_upload(const UploadArgs &a, int n_pairs, cudaStream_t st);
+
 
 // ---------------------------------------------------------------- adjoint --
 

@@ -305,16 +305,16 @@ class Scheduler:
 
 # ------------------------------------------------------------- GPU executor --
 
-def warm_config(W: int, H: int, bits: int, precision: str = "fp32", max_batch: int = 64):
+def warm_config(W: int, H: int, bits: int, precision: str = "fp32", max_batch: int = 64, host_frames: bool = False):
     from .binding import Config
     return Config(W, H, windows=(16,), overlaps=(0.5,), radii=(4,), levels=0, bit_depth=bits,
-                  precision=precision, max_batch=max_batch)
+                  precision=precision, max_batch=max_batch, host_frames=host_frames)
 
 
-def cold_config(W: int, H: int, bits: int, precision: str = "fp32", max_batch: int = 64):
+def cold_config(W: int, H: int, bits: int, precision: str = "fp32", max_batch: int = 64, host_frames: bool = False):
     from .binding import Config
     return Config(W, H, windows=(32, 16), overlaps=(0.5, 0.5), radii=(4, 4), levels=2, bit_depth=bits,
-                  precision=precision, max_batch=max_batch)
+                  precision=precision, max_batch=max_batch, host_frames=host_frames)
 
 
 class GpuExecutor(Executor):
@@ -322,10 +322,16 @@ class GpuExecutor(Executor):
     CUDA stream per slot, so batches in different slots overlap."""
 
     def __init__(self, slots: int, precision: str = "fp32", max_batch: int = 64, cold_batch: int = 8,
-                 device: int = 0, max_megapixels: float = 16.0, prewarm: bool = False, alpha1=None, alpha2=None):
+                 device: int = 0, max_megapixels: float = 16.0, prewarm: bool = False, alpha1=None, alpha2=None,
+                 host_frames: bool = True):
         import torch
         self.torch = torch
         self.precision = precision
+        # requests carry pinned host frames: the engines read them with their
+        # upload kernel (inside the captured graph) instead of one copy call
+        # per image from this thread, which bounds how many batches a second
+        # the scheduler can start
+        self.host_frames = host_frames
         self.max_batch = max_batch
         self.cold_batch = cold_batch
         # pixels per launch are capped so that a batch of large frames holds
@@ -353,7 +359,7 @@ class GpuExecutor(Executor):
     def _cfg(self, key: Key, mode: str):
         W, H, bits = key
         f = warm_config if mode == WARM else cold_config
-        return f(W, H, bits, self.precision, self.max_pairs(key, mode))
+        return f(W, H, bits, self.precision, self.max_pairs(key, mode), self.host_frames)
 
     def drop_engine(self, key: Key, mode: str, slot: int) -> None:
         e = self.engines.pop((key, mode, slot), None)
@@ -376,7 +382,8 @@ class GpuExecutor(Executor):
         dt = torch.uint8 if bits == 8 else torch.int16
         st = self.streams[slot]
         with torch.cuda.stream(st):
-            a = torch.zeros((H, W), dtype=dt, device=self.device)
+            a = (torch.zeros((H, W), dtype=dt).pin_memory() if self.host_frames
+                 else torch.zeros((H, W), dtype=dt, device=self.device))
             pu = torch.zeros((eng.ny, eng.nx), dtype=torch.float32, device=self.device)
             for n in range(1, self.max_pairs(key, mode) + 1):
                 outs = eng.empty_outputs(n)
@@ -392,21 +399,28 @@ class GpuExecutor(Executor):
         # cold schedule, per-stage fields (an upper estimate of rpiv_workspace_bytes)
         pix = (W + 48) * (H + 16)
         per_pair = 4 * pix + (2 * 4 * (W * H // 4 + W * H // 16) if mode == COLD else 0) + 64 * (W * H // 64)
+        if self.host_frames:
+            per_pair += 2 * (W + 16) * H * (1 if bits == 8 else 2)  # the uploaded frames
         return per_pair * self.max_pairs(key, mode)
 
     def request_bytes(self, key: Key) -> int:
         W, H, bits = key
         bpp = 1 if bits == 8 else 2
         nx, ny = (W - 16) // 8 + 1, (H - 16) // 8 + 1
-        return 2 * W * H * bpp + nx * ny * 13
+        # device copies of the frames (unless the engine uploads them itself) and the fields
+        return (0 if self.host_frames else 2 * W * H * bpp) + nx * ny * 13
 
     def submit(self, slot, key, mode, reqs, preds):
         torch = self.torch
         eng = self._engine(key, mode, slot)
         st = self.streams[slot]
         with torch.cuda.stream(st):
-            a = [r.payload[0].to(self.device, non_blocking=True) for r in reqs]
-            b = [r.payload[1].to(self.device, non_blocking=True) for r in reqs]
+            if self.host_frames:
+                a = [r.payload[0] for r in reqs]
+                b = [r.payload[1] for r in reqs]
+            else:
+                a = [r.payload[0].to(self.device, non_blocking=True) for r in reqs]
+                b = [r.payload[1].to(self.device, non_blocking=True) for r in reqs]
             outs = eng.empty_outputs(len(reqs))
             if len(reqs) == 1:
                 outs = tuple(o.unsqueeze(0) for o in outs)

@@ -81,6 +81,40 @@ def test_unknown_enum_and_null_rejected(lib):
     assert lib.rpiv_create(None, 0, None) == 1
 
 
+def test_binding_config_mirrors_the_header_struct(lib, tmp_path):
+    # the ctypes mirror must have the C struct's size and field offsets
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    inc = os.path.join(ROOT, "include")
+    cuda_inc = next((d for d in ("/usr/local/cuda/include",) if os.path.isdir(d)), None)
+    if cuda_inc is None:
+        pytest.skip("CUDA headers not found")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "rpiv.h"\n'
+                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(rpiv_config), '
+                   'offsetof(rpiv_config, max_batch), offsetof(rpiv_config, host_frames)); return 0; }\n')
+    exe = tmp_path / "sz"
+    subprocess.run([cc, "-I", inc, "-I", cuda_inc, str(src), "-o", str(exe)], check=True)
+    size, off_mb, off_hf = (int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                            check=True).stdout.split())
+    assert ctypes.sizeof(binding._Config) == size
+    assert binding._Config.max_batch.offset == off_mb and binding._Config.host_frames.offset == off_hf
+
+
+def test_host_frames_flag_default_and_range(lib):
+    c = binding._Config()
+    assert lib.rpiv_config_default(ctypes.byref(c)) == 0
+    assert c.host_frames == 0
+    c = rp.Config(256, 256, (32,), (0.5,), (4,), host_frames=True).to_c()
+    assert c.host_frames == 1 and lib.rpiv_validate_config(ctypes.byref(c), None, None) == 0
+    c.host_frames = 2
+    assert lib.rpiv_validate_config(ctypes.byref(c), None, None) == 1
+    assert b"host_frames" in lib.rpiv_last_error()
+
+
 def test_create_without_device_reports_no_device(lib):
     import torch
     if torch.cuda.is_available():

@@ -101,3 +101,47 @@ def test_stage_bounded_wait_runs_out_and_is_reported(stall, precision, tc, monke
     rp.stage_status()
     valid = rp.decode_info(info)[0]
     assert float(valid.float().mean()) > 0.99
+
+
+@pytest.mark.parametrize("W,H,bits,levels", [(256, 256, 8, 1), (250, 198, 12, 0)])
+def test_host_frames_equal_device_frames(W, H, bits, levels):
+    """An engine built with host_frames reads pinned host images through its
+    upload kernel; its fields equal a device-frames engine's bit for bit, on
+    the eager first call and on graph replays, with and without a predictor.
+    250 x 198 u16 rows (500 bytes) are not 16-byte multiples: the upload's
+    byte path."""
+    import synth
+    flow = synth.Flow(U=3.3, V=-1.7, vortices=[(0.5 * W, 0.5 * H, 200.0, 20.0)])
+    pairs = [synth.render_pair(synth.ImageSpec(W=W, H=H, bit_depth=bits, ppp=0.05, dp=(2.5, 2.5), seed=6100 + k), flow)
+             for k in range(3)]
+    kw = dict(windows=(32, 16), overlaps=(0.5, 0.5), radii=(4, 4), levels=levels, bit_depth=bits, max_batch=3)
+    dev_eng = rp.Engine(rp.Config(W, H, **kw))
+    host_eng = rp.Engine(rp.Config(W, H, host_frames=True, **kw))
+    dev = [(rp.to_device(A), rp.to_device(B)) for A, B in pairs]
+    host = [(rp.to_device(A, "cpu", pin=True), rp.to_device(B, "cpu", pin=True)) for A, B in pairs]
+    assert all(t.is_pinned() for p in host for t in p)
+    ref = dev_eng.process_batch([p[0] for p in dev], [p[1] for p in dev])
+    pred = (ref[0][0].clone(), ref[1][0].clone())
+    for rep in range(2):  # eager first call, then the captured graph
+        got = host_eng.process_batch([p[0] for p in host], [p[1] for p in host])
+        torch.cuda.synchronize()
+        for k in range(4):
+            assert torch.equal(got[k], ref[k]), (rep, k)
+    r1 = dev_eng.process_pair(dev[1][0], dev[1][1], pred=pred)
+    g1 = host_eng.process_pair(host[1][0], host[1][1], pred=pred)
+    torch.cuda.synchronize()
+    for k in range(4):
+        assert torch.equal(g1[k], r1[k]), k
+    # device images are refused by a host_frames engine, in the binding and in the library
+    with pytest.raises(ValueError):
+        host_eng.process_pair(dev[0][0], dev[0][1])
+    import ctypes
+    u, v, w, m = host_eng.empty_outputs(1)
+    arr = ctypes.c_void_p * 1
+    st = binding.load().rpiv_process_batch(host_eng.handle, 1, arr(dev[0][0].data_ptr()), arr(dev[0][1].data_ptr()),
+                                           dev[0][0].stride(0) * dev[0][0].element_size(), None, None,
+                                           arr(u.data_ptr()), arr(v.data_ptr()), None, None,
+                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 1 and b"page-locked" in binding.load().rpiv_last_error()
+    dev_eng.close()
+    host_eng.close()
