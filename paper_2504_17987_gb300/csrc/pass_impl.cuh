@@ -252,7 +252,7 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 __device__ __forceinline__ int tc_front(int R) { return max(0, 8 * ((2 * R + 8) / 8) - 1 - 2 * R); }
 __device__ __forceinline__ int tc_slab_row(int R, int rows, int j) { return tc_front(R) + 2 * R + j * (rows + 2 * R); }
 
-// Strip loads on the bulk path (steps that are multiples of 4): warp 0 issues
+// Strip loads on the bulk path (steps that are multiples of 4): one warp issues
 // the copies of a step's regions without waiting, so that they overlap the end
 // of the previous step; step k completes phase k of the barrier.
 static __device__ __forceinline__ void issue_regions(const PassArgs &a, const TileGeom &g, int pair, float *As, float *Bs,
@@ -1451,8 +1451,10 @@ __global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(c
         stencil_direct(a, g, As, Bs, ws);
         __syncthreads();
         // the regions are read no more in this step: the next step's copies go
-        // out now, behind the CTA barrier that ordered the reads
-        if (wy + 1 < wy_end && threadIdx.x < 32) {
+        // out now, behind the CTA barrier that ordered the reads, from warp 1,
+        // so that they do not wait for the fit that warp 0's first lanes run
+        // (warp 0 initialised the barrier before the loop and waits on it)
+        if (wy + 1 < wy_end && threadIdx.x >= 32 && threadIdx.x < 64) {
             TileGeom gn = g;
             gn.wy0 = wy + 1;
             gn.ay0 = (wy + 1) * s;
