@@ -540,6 +540,23 @@ static __device__ __forceinline__ void window_stats(const PassArgs &a, const Til
 // quarter-warp reads consecutive shifts (bank-conflict free) and a butterfly of
 // shuffles over lane distances 32 / RG, ... , 16 sums a unit's partials; row
 // group 0 stores the sum.
+// Packed pairs of FP32 values for the paired FMA (fma.rn.f32x2: two IEEE
+// FMAs in one instruction, each rounded as fmaf).
+__device__ __forceinline__ uint64_t pack_f2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_f2(uint64_t p) { return __uint_as_float((uint32_t)p); }
+__device__ __forceinline__ float hi_f2(uint64_t p) { return __uint_as_float((uint32_t)(p >> 32)); }
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 template <int ND>
 __device__ __forceinline__ void sum_row_groups(float (&acc)[ND], int lrg)
 {
@@ -574,14 +591,22 @@ __device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileG
         const int syi = u - (b - b0) * ND;
         const int byi = b / g.nbx, bxi = b - byi * g.nbx;
         const int c0 = bxi * G, r0 = byi * G + gi * rows;
-        float acc[ND];
+        // Two accumulator sets of packed pairs, so that every pair of B' values
+        // an FMA pair reads is an aligned register pair of a 128-bit load: for
+        // the columns j with MIS + j even, set E holds (d, d + 1) for even d
+        // and a single d = ND - 1; otherwise set O holds a single d = 0 and the
+        // pairs (d, d + 1) for odd d.  acc[d] = E[d] + O[d].
+        constexpr int NPR = (ND - 1) / 2;
+        uint64_t pe[NPR > 0 ? NPR : 1], po[NPR > 0 ? NPR : 1];
+        float se = 0.f, so = 0.f;
 #pragma unroll
-        for (int d = 0; d < ND; ++d) acc[d] = 0.f;
+        for (int q = 0; q < NPR; ++q) pe[q] = po[q] = 0ull;
         for (int y = r0; y < r0 + rows; ++y) {
             const float *arow = As + y * P.a_pitch;
             const float *brow = Bs + (y + syi + 1) * P.b_pitch + P.padl - R - MIS;
             for (int c = c0; c < c0 + G; c += 4) {
                 const float4 a4 = *reinterpret_cast<const float4 *>(arow + c);
+                uint64_t bp[NQ * 2];
                 float bv[NQ * 4];
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
@@ -590,14 +615,37 @@ __device__ __forceinline__ void block_planes_fp32(const PassArgs &a, const TileG
                     bv[4 * q + 1] = t.y;
                     bv[4 * q + 2] = t.z;
                     bv[4 * q + 3] = t.w;
+                    bp[2 * q] = pack_f2(t.x, t.y);
+                    bp[2 * q + 1] = pack_f2(t.z, t.w);
                 }
                 const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    const uint64_t a2 = pack_f2(av[j], av[j]);
+                    if (((MIS + j) & 1) == 0) {
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) acc[d] = fmaf(av[j], bv[MIS + j + d], acc[d]);
+                        for (int q = 0; q < NPR; ++q) pe[q] = ffma2(a2, bp[(MIS + j) / 2 + q], pe[q]);
+                        se = fmaf(av[j], bv[MIS + j + ND - 1], se);
+                    } else {
+                        so = fmaf(av[j], bv[MIS + j], so);
+#pragma unroll
+                        for (int q = 0; q < NPR; ++q) po[q] = ffma2(a2, bp[(MIS + j + 1) / 2 + q], po[q]);
+                    }
                 }
             }
+        }
+        float acc[ND];
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) {
+            acc[2 * q] = lo_f2(pe[q]);
+            acc[2 * q + 1] = hi_f2(pe[q]);
+        }
+        acc[ND - 1] = se;
+        acc[0] += so;
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) {
+            acc[2 * q + 1] += lo_f2(po[q]);
+            acc[2 * q + 2] += hi_f2(po[q]);
         }
         sum_row_groups<ND>(acc, lrg);
         if (base + ul < units && gi == 0) {
