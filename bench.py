@@ -611,31 +611,39 @@ def run_adjoint(args):
 def measure_fma_peak(index: int, reps: int = 30) -> dict:
     """The FP32 CUDA-core peak measured by the FMA-throughput microbenchmark
     (libfmapeak: 16 independent FMA chains per thread, 8 CTAs of 256 threads on
-    every SM), the shortest of `reps` launches, with the SM clock sampled while
-    it runs; also the rate per SM and clock, to compare with the 128 FP32 lanes
-    x 2 flop of the architecture."""
+    every SM, as scalar FMAs and as packed fma.rn.f32x2 pairs), the shortest of
+    `reps` launches of each, with the SM clock sampled while they run; the
+    peak is the faster form.  Also the rate per SM and clock, to compare with
+    the 128 FP32 lanes x 2 flop of the architecture."""
     import ctypes
 
     import torch
 
     from paper_2504_17987_gb300 import build as b
     lib = ctypes.CDLL(b.build_fma_peak())
-    lib.fma_peak_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
-                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
-    best, flops = ctypes.c_float(), ctypes.c_double()
+    lib.fma_peak_run2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     st = torch.cuda.current_stream()
+    forms = {}
     with ClockSampler(index) as cs:
         cs.mark_start()
-        rc = lib.fma_peak_run(8, 8192, reps, ctypes.byref(best), ctypes.byref(flops), ctypes.c_void_p(st.cuda_stream))
+        for packed in (0, 1):
+            best, flops = ctypes.c_float(), ctypes.c_double()
+            rc = lib.fma_peak_run2(8, 8192 if not packed else 4096, reps, packed, ctypes.byref(best),
+                                   ctypes.byref(flops), ctypes.c_void_p(st.cuda_stream))
+            if rc != 0:
+                raise RuntimeError(f"FMA microbenchmark failed: CUDA error {rc}")
+            forms["packed" if packed else "scalar"] = (best.value, flops.value)
         cs.mark_end()
-    if rc != 0:
-        raise RuntimeError(f"FMA microbenchmark failed: CUDA error {rc}")
     clk = cs.summary()
     sms = torch.cuda.get_device_properties(index).multi_processor_count
-    tflops = flops.value / (best.value / 1e3) / 1e12
+    rates = {k: f / (ms / 1e3) / 1e12 for k, (ms, f) in forms.items()}
+    top = max(rates, key=rates.get)
+    tflops = rates[top]
     mhz = (clk or {}).get("sm_mhz") or None
     per_clk = (tflops * 1e12 / (sms * mhz * 1e6)) if mhz else None
-    return {"tflops": tflops, "best_ms": best.value, "flops_per_launch": flops.value, "sms": sms,
+    return {"tflops": tflops, "form": top, "scalar_tflops": rates["scalar"], "packed_tflops": rates["packed"],
+            "best_ms": forms[top][0], "flops_per_launch": forms[top][1], "sms": sms,
             "flop_per_sm_per_clock": per_clk, "clocks": clk}
 
 
@@ -969,7 +977,8 @@ def main():
     fma = measure_fma_peak(local)
     if head == "fp32":
         bound, peak = "alu", fma["tflops"]
-        peak_src = (f"measured: FMA microbenchmark {fma['tflops']:.1f} TFLOP/s at "
+        peak_src = (f"measured: FMA microbenchmark {fma['tflops']:.1f} TFLOP/s ({fma['form']} FMAs; scalar "
+                    f"{fma['scalar_tflops']:.1f}, packed f32x2 {fma['packed_tflops']:.1f}) at "
                     f"{(fma['clocks'] or {}).get('sm_mhz')} MHz (derived {sms} SMs x 128 lanes x 2 x "
                     f"{sm_max:.0f} MHz = {fp32_derived:.1f})")
     else:

@@ -2,7 +2,10 @@
 // pipe that the FP32 correlation pass is reported against (the ALU roofline).
 // Every thread runs 16 independent FMA chains (enough in flight to cover the
 // pipe's latency at full occupancy); the launch fills every SM with 8 CTAs of
-// 256 threads.  Measurement support, built as its own small library.
+// 256 threads.  A second kernel runs the chains as packed pairs (fma.rn.f32x2,
+// two FMAs per instruction), which the paired plane loop of the pass uses: the
+// peak is the faster of the two.  Measurement support, built as its own small
+// library.
 #include <cstdio>
 
 #include <cuda_runtime.h>
@@ -26,12 +29,36 @@ __global__ void __launch_bounds__(256) fma_kernel(float *out, int iters, float x
     if (s == -1.f) out[blockIdx.x] = s;  // keeps the chains live; never true for these inputs
 }
 
+// The same chains as packed pairs: fma.rn.f32x2, two FMAs per instruction.
+__global__ void __launch_bounds__(256) fma2_kernel(float *out, int iters, float x, float y)
+{
+    unsigned long long a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+        const float lo = (float)threadIdx.x * 1e-3f + (float)j, hi = lo + 0.5f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(a[j]) : "f"(lo), "f"(hi));
+    }
+    unsigned long long x2, y2;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(x2) : "f"(x));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(y2) : "f"(y));
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[j]) : "l"(x2), "l"(y2));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j)
+        s += __uint_as_float((unsigned)a[j]) + __uint_as_float((unsigned)(a[j] >> 32));
+    if (s == -1.f) out[blockIdx.x] = s;  // keeps the chains live; never true for these inputs
+}
+
 }  // namespace
 
 // Runs the kernel `reps` times on `stream` (after one warm-up launch) and
 // returns the shortest launch in *best_ms and the FP32 flops of one launch in
 // *flops (2 per FMA).  Returns 0, or a CUDA error code.
-extern "C" int fma_peak_run(int blocks_per_sm, int iters, int reps, float *best_ms, double *flops, void *stream)
+extern "C" int fma_peak_run2(int blocks_per_sm, int iters, int reps, int packed, float *best_ms, double *flops,
+                             void *stream)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -45,10 +72,14 @@ extern "C" int fma_peak_run(int blocks_per_sm, int iters, int reps, float *best_
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    fma_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-6f);
+    auto launch = [&] {
+        if (packed) fma2_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-6f);
+        else fma_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-6f);
+    };
+    launch();
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
         cudaEventRecord(e0, st);
-        fma_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-6f);
+        launch();
         cudaEventRecord(e1, st);
         e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -60,6 +91,12 @@ extern "C" int fma_peak_run(int blocks_per_sm, int iters, int reps, float *best_
     cudaEventDestroy(e1);
     cudaFree(out);
     *best_ms = best;
-    *flops = 2.0 * kChains * (double)iters * 256.0 * (double)blocks;
+    *flops = 2.0 * kChains * (double)iters * 256.0 * (double)blocks * (packed ? 2.0 : 1.0);
     return (int)e;
+}
+
+// Scalar FMA chains (fma_peak_run2 with packed = 0).
+extern "C" int fma_peak_run(int blocks_per_sm, int iters, int reps, float *best_ms, double *flops, void *stream)
+{
+    return fma_peak_run2(blocks_per_sm, iters, reps, 0, best_ms, flops, stream);
 }

@@ -376,6 +376,23 @@ __device__ __forceinline__ float inv_norm(float s1, float s2, float inv_n, float
     return EB > tau ? rsqrtf(EB) : 0.f;
 }
 
+// Packed pairs of FP32 values for the paired FMA (fma.rn.f32x2: two IEEE
+// FMAs in one instruction, each rounded as fmaf).
+__device__ __forceinline__ uint64_t pack_f2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_f2(uint64_t p) { return __uint_as_float((uint32_t)p); }
+__device__ __forceinline__ float hi_f2(uint64_t p) { return __uint_as_float((uint32_t)(p >> 32)); }
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Window box sums of B' and B'^2 at every shift, in two sliding passes:
 //   C[r][x] = sum_{y=r}^{r+w-1} B'[y][x]        (threads along x: conflict free)
 //   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]         (threads along r, odd pitch)
@@ -540,23 +557,6 @@ static __device__ __forceinline__ void window_stats(const PassArgs &a, const Til
 // quarter-warp reads consecutive shifts (bank-conflict free) and a butterfly of
 // shuffles over lane distances 32 / RG, ... , 16 sums a unit's partials; row
 // group 0 stores the sum.
-// Packed pairs of FP32 values for the paired FMA (fma.rn.f32x2: two IEEE
-// FMAs in one instruction, each rounded as fmaf).
-__device__ __forceinline__ uint64_t pack_f2(float lo, float hi)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float lo_f2(uint64_t p) { return __uint_as_float((uint32_t)p); }
-__device__ __forceinline__ float hi_f2(uint64_t p) { return __uint_as_float((uint32_t)(p >> 32)); }
-__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 template <int ND>
 __device__ __forceinline__ void sum_row_groups(float (&acc)[ND], int lrg)
 {
