@@ -191,6 +191,26 @@ def validate_config(cfg: Config) -> Tuple[int, int]:
     return nx.value, ny.value
 
 
+_PTR_ARRAYS = {}
+
+
+def _ptr_array(n: int):
+    """ctypes array type of n pointers (one type per n, made once)."""
+    t = _PTR_ARRAYS.get(n)
+    if t is None:
+        t = _PTR_ARRAYS[n] = ctypes.c_void_p * n
+    return t
+
+
+def _entry_ptrs(x, n: int):
+    """Addresses of the n per-pair outputs: rows of one contiguous (n, ...)
+    tensor by stride arithmetic, or the entries of a list."""
+    if isinstance(x, torch.Tensor) and x.dim() >= 1 and x.shape[0] == n:
+        base, step = x.data_ptr(), x.stride(0) * x.element_size()
+        return [base + i * step for i in range(n)]
+    return [x[i].data_ptr() for i in range(n)]
+
+
 def _img_check(t: torch.Tensor, cfg_fmt: int, host: bool = False):
     if host:
         if t.is_cuda or not t.is_pinned():
@@ -247,10 +267,12 @@ class Engine:
         return b.value
 
     def empty_outputs(self, n: int = 1):
+        """(u, v, vort, mask) for n pairs: u, v and vort are views of one float
+        allocation (two allocations instead of four per call)."""
         dev = torch.device("cuda", self.device)
         shp = (n, self.ny, self.nx) if n > 1 else (self.ny, self.nx)
-        return (torch.empty(shp, dtype=torch.float32, device=dev), torch.empty(shp, dtype=torch.float32, device=dev),
-                torch.empty(shp, dtype=torch.float32, device=dev), torch.empty(shp, dtype=torch.uint8, device=dev))
+        f = torch.empty((3,) + shp, dtype=torch.float32, device=dev)
+        return f[0], f[1], f[2], torch.empty(shp, dtype=torch.uint8, device=dev)
 
     def process_pair(self, a: torch.Tensor, b: torch.Tensor, pred=None, out=None, stream=None):
         """Returns (u, v, vort, mask) on the final-pass grid (asynchronous)."""
@@ -281,13 +303,13 @@ class Engine:
             if n == 1:
                 outs = tuple(o.unsqueeze(0) for o in outs)
         u, v, w, m = outs
-        arr = ctypes.c_void_p * n
+        arr = _ptr_array(n)
         A = arr(*[t.data_ptr() for t in a_list])
         B = arr(*[t.data_ptr() for t in b_list])
-        U = arr(*[u[i].data_ptr() for i in range(n)])
-        V = arr(*[v[i].data_ptr() for i in range(n)])
-        Wv = arr(*[w[i].data_ptr() for i in range(n)]) if w is not None else None
-        M = arr(*[m[i].data_ptr() for i in range(n)]) if m is not None else None
+        U = arr(*_entry_ptrs(u, n))
+        V = arr(*_entry_ptrs(v, n))
+        Wv = arr(*_entry_ptrs(w, n)) if w is not None else None
+        M = arr(*_entry_ptrs(m, n)) if m is not None else None
         PU = PV = None
         if preds is not None and any(p is not None for p in preds):
             PU = arr(*[(p[0].data_ptr() if p is not None else None) for p in preds])

@@ -349,6 +349,7 @@ class GpuExecutor(Executor):
         self.out_state = {}
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self.slot_events = [torch.cuda.Event() for _ in range(slots)]
         self.engines = {}
 
     def max_pairs(self, key: Key, mode: str) -> int:
@@ -432,7 +433,9 @@ class GpuExecutor(Executor):
                     pr[1].record_stream(st)
             eng.process_batch(a, b, preds=p, outs=outs, stream=st)
             smoothed = self._smooth(reqs, outs, st)
-            ev = torch.cuda.Event()
+            # one event per slot: a slot runs one batch at a time, so its event
+            # is free again once the batch it marked has been polled complete
+            ev = self.slot_events[slot]
             ev.record(st)
         return (ev, outs, a, b, p, smoothed)
 
