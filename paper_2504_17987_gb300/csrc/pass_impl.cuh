@@ -6,17 +6,17 @@
 // Work of one CTA, staged in shared memory:
 //   A region   raw A over the union of the tile's windows (aw x ah)
 //   B' region  raw B' over the A region grown by R+1 on each side
-//   C, V       sliding box sums of B' and B'^2 (C: columns, V: rows); V1[r][c]
-//              is the sum of B' over the w x w box with top-left logical B'
-//              pixel (r, c), VN[r][c] = 1 / sqrt(E_B) of that box (0 when the
-//              box is degenerate), i.e. every window at every shift in
-//              [-R-1, R+1]^2, by lookup
+//   C, V       sliding box sums of B' and B'^2 (C: columns, V: rows), pairs
+//              of floats; V[r][c] = (S1, 1 / sqrt(E_B)) of the w x w box with
+//              top-left logical B' pixel (r, c): its sum of B' and its inverse
+//              norm (0 when the box is degenerate), i.e. every window at every
+//              shift in [-R-1, R+1]^2, by lookup
 //   P          block planes: the A region is cut into G x G blocks
 //              (G = gcd(w, s)); P_b(s) = sum_{x in b} A(x) B'(x + s).
 //              A window's numerator is the sum of its (w/G)^2 block planes
-//              minus mean(A) * V1(s); this regrouping is exact, and computes
+//              minus mean(A) * S1(s); this regrouping is exact, and computes
 //              each block once instead of once per overlapping window.
-// The peak is searched on C(s) sqrt(E_A) = numerator(s) VN(s): a positive
+// The peak is searched on C(s) sqrt(E_A) = numerator(s) / sqrt(E_B(s)): a positive
 // per-window scale leaves the argmax unchanged; the five stencil values are
 // scaled back by 1 / sqrt(E_A) before the fit.
 // The planes are formed with FP32 FMAs on the CUDA cores, or with BF16/FP16
@@ -369,15 +369,19 @@ __device__ __forceinline__ void tc_copies(const PassArgs &a, const TileGeom &g, 
 
 // ------------------------------------------------------ box sums (C, V) --
 
-// 1 / sqrt(E_B) of a box from its sum and sum of squares; 0 for a degenerate box
+// 1 / sqrt(E_B) of a box from its sum and sum of squares; 0 for a degenerate
+// box.  E_B > tau > 0 is a normal float, so the hardware's approximate
+// reciprocal square root needs no subnormal handling (flush-to-zero form).
 __device__ __forceinline__ float inv_norm(float s1, float s2, float inv_n, float tau)
 {
     const float EB = s2 - s1 * s1 * inv_n;
-    return EB > tau ? rsqrtf(EB) : 0.f;
+    float r = 0.f;
+    if (EB > tau) asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(EB));
+    return r;
 }
 
-// Packed pairs of FP32 values for the paired FMA (fma.rn.f32x2: two IEEE
-// FMAs in one instruction, each rounded as fmaf).
+// Packed pairs of FP32 values for the paired arithmetic (fma/add/sub.rn.f32x2:
+// two IEEE operations in one instruction, each rounded as the scalar one).
 __device__ __forceinline__ uint64_t pack_f2(float lo, float hi)
 {
     uint64_t r;
@@ -392,21 +396,35 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // Window box sums of B' and B'^2 at every shift, in two sliding passes:
-//   C[r][x] = sum_{y=r}^{r+w-1} B'[y][x]        (threads along x: conflict free)
-//   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]         (threads along r, odd pitch)
-// so V[r][c] is the sum over the w x w box whose top-left logical B' pixel
-// is (r, c); the second plane keeps 1 / sqrt(E_B) of the box instead of its
-// sum of squares.  Each thread keeps a running sum over box_lv (columns) or
-// box_lh (rows) outputs; the plan sets them and the number of runs for a full
-// tile, and an edge tile, never larger, skips the runs that start past its end.
+//   C[r][x] = sum_{y=r}^{r+w-1} (B'[y][x], B'[y][x]^2)   (threads along x: conflict free)
+//   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]                  (threads along r, odd pitch)
+// so V[r][c] sums the w x w box whose top-left logical B' pixel is (r, c); its
+// second member keeps 1 / sqrt(E_B) of the box instead of its sum of squares.
+// C and V hold (S1, S2) and (S1, 1 / sqrt(E_B)) pairs: one 64-bit access per
+// element, and the row pass adds both sums with one paired instruction.  Each
+// thread keeps a running sum over box_lv (columns) or box_lh (rows) outputs;
+// the plan sets them and the number of runs for a full tile, and an edge tile,
+// never larger, skips the runs that start past its end.
 static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
 {
     const PassPlan &P = a.plan;
     const int w = g.w, tid = threadIdx.x;
-    const int cp = P.h_pitch;  // pitch of C and V (odd)
-    float *C1 = Cs, *C2 = Cs + g.vh * cp;
+    const int cp = P.h_pitch;  // pitch of C in pairs (odd)
+    float2 *C = reinterpret_cast<float2 *>(Cs);
     const int Lv = P.box_lv;
     for (int it = tid; it < g.BC * P.box_nv; it += blockDim.x) {
         const int seg = it / g.BC, x = it - seg * g.BC;
@@ -419,38 +437,32 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
             s1 += b;
             s2 = fmaf(b, b, s2);
         }
-        C1[r_lo * cp + x] = s1;
-        C2[r_lo * cp + x] = s2;
+        C[r_lo * cp + x] = make_float2(s1, s2);
         for (int r = r_lo + 1; r < r_hi; ++r) {
             const float bo = col[(r - 1) * P.b_pitch], bi = col[(r + w - 1) * P.b_pitch];
             s1 += bi - bo;
             s2 += bi * bi - bo * bo;
-            C1[r * cp + x] = s1;
-            C2[r * cp + x] = s2;
+            C[r * cp + x] = make_float2(s1, s2);
         }
     }
     __syncthreads();
-    const int vp = P.v_pitch;  // pitch of V (odd, >= hw)
+    const int vp = P.v_pitch;  // pitch of V in pairs (odd, >= hw)
     const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
-    float *V1 = Vs, *VN = Vs + g.vh * vp;
+    float2 *V = reinterpret_cast<float2 *>(Vs);
+    const uint64_t *Cp = reinterpret_cast<const uint64_t *>(Cs);
     const int Lh = P.box_lh;
     for (int it = tid; it < g.vh * P.box_nh; it += blockDim.x) {
         const int seg = it / g.vh, r = it - seg * g.vh;
         const int c_lo = seg * Lh, c_hi = min(g.hw, c_lo + Lh);
         if (c_lo >= g.hw) continue;
-        const float *c1 = C1 + r * cp, *c2 = C2 + r * cp;
-        float s1 = 0.f, s2 = 0.f;
-        for (int x = c_lo; x < c_lo + w; ++x) {
-            s1 += c1[x];
-            s2 += c2[x];
-        }
-        V1[r * vp + c_lo] = s1;
-        VN[r * vp + c_lo] = inv_norm(s1, s2, inv_n, tau);
+        const uint64_t *cr = Cp + r * cp;
+        float2 *vr = V + r * vp;
+        uint64_t s = 0ull;  // (S1, S2), +0
+        for (int x = c_lo; x < c_lo + w; ++x) s = fadd2(s, cr[x]);
+        vr[c_lo] = make_float2(lo_f2(s), inv_norm(lo_f2(s), hi_f2(s), inv_n, tau));
         for (int c = c_lo + 1; c < c_hi; ++c) {
-            s1 += c1[c + w - 1] - c1[c - 1];
-            s2 += c2[c + w - 1] - c2[c - 1];
-            V1[r * vp + c] = s1;
-            VN[r * vp + c] = inv_norm(s1, s2, inv_n, tau);
+            s = fadd2(s, fsub2(cr[c + w - 1], cr[c - 1]));
+            vr[c] = make_float2(lo_f2(s), inv_norm(lo_f2(s), hi_f2(s), inv_n, tau));
         }
     }
 }
@@ -987,7 +999,7 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
     const int ps = ONE_PLANE ? NP : P.pstride, rs = g.nbx * ps;
     const float tau = TAU_PER_PIXEL * (float)(g.w * g.w);
     const int cp = P.v_pitch;
-    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    const float2 *VV = reinterpret_cast<const float2 *>(Vs);
     constexpr uint32_t NONE = 0xffffffffu;
     // shifts owned by this lane: plane offset q and box-sum offset, per j
     constexpr int NQ = RC >= 0 ? ((2 * RC + 1) * (2 * RC + 1) + 31) / 32 : 1;
@@ -1026,8 +1038,7 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
             continue;
         }
         const float *pb = Ps + ((ring_wy < 0 ? wyi * sg * g.nbx : 0) + wxi * sg) * ps;
-        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
-        const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float2 *vb = VV + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
         float best = 0.f;
         uint32_t bq = NONE;
         // ascending q: the first of equal values stays; NaN never wins
@@ -1041,12 +1052,12 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
 #pragma unroll
             for (int j = 0; j < NQ; ++j) {
                 if (j < NQ - 1 || lane + 32 * j < NP)
-                    offer(coef(block_sum(pb, qv[j]), muA, v1[vv[j]], vn[vv[j]]), qv[j]);
+                    offer(coef(block_sum(pb, qv[j]), muA, vb[vv[j]].x, vb[vv[j]].y), qv[j]);
             }
         } else {
             for (int q = lane; q < NP; q += 32) {
                 const int qy = q / ND, vo = (qy - R) * cp + (q - qy * ND - R);
-                offer(coef(block_sum(pb, q), muA, v1[vo], vn[vo]), q);
+                offer(coef(block_sum(pb, q), muA, vb[vo].x, vb[vo].y), q);
             }
         }
         const uint32_t key = bq == NONE ? 0u : ord_key(best);
@@ -1062,7 +1073,7 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
             float c = 0.f;
             if (!direct) {
                 const int q = (sy + R) * ND + (sx + R), vo = sy * cp + sx;
-                c = scaled_zncc(block_sum(pb, q), muA, v1[vo], vn[vo]);
+                c = scaled_zncc(block_sum(pb, q), muA, vb[vo].x, vb[vo].y);
             }
             ws.c5[wi * 5 + lane] = c;
             const unsigned bits = __ballot_sync(0x1fu, direct);
@@ -1095,7 +1106,7 @@ static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, c
     const int ps = NP, rs = g.nbx * ps;
     const float tau = TAU_PER_PIXEL * (float)(g.w * g.w);
     const int cp = P.v_pitch;
-    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    const float2 *VV = reinterpret_cast<const float2 *>(Vs);
     int qv[NQ], vv[NQ];
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
@@ -1121,15 +1132,14 @@ static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, c
         const float muA = stats[2 * wic], EA = stats[2 * wic + 1];
         const bool live = has && EA > tau;  // degenerate windows: finalize passes the predictor
         const float *pb = Ps + ((ring_wy < 0 ? wyi * sg * g.nbx : 0) + wxi * sg) * ps;
-        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
-        const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float2 *vb = VV + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
         float best = 0.f;
         uint32_t bq = NONE;
         if (live) {
 #pragma unroll
             for (int j = 0; j < NQ; ++j) {
                 if (j < NQ - 1 || hl + 16 * j < NP) {
-                    const float c = scaled_zncc(block_sum(pb, qv[j]), muA, v1[vv[j]], vn[vv[j]]);
+                    const float c = scaled_zncc(block_sum(pb, qv[j]), muA, vb[vv[j]].x, vb[vv[j]].y);
                     // ascending q: the first of equal values stays; NaN never wins
                     if (c > best || (bq == NONE && c == c)) {
                         best = c;
@@ -1157,7 +1167,7 @@ static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, c
             direct = !(sy >= -R && sy <= R && sx >= -R && sx <= R);
             if (!direct) {
                 const int q = (sy + R) * ND + (sx + R), vo = sy * cp + sx;
-                c = scaled_zncc(block_sum(pb, q), muA, v1[vo], vn[vo]);
+                c = scaled_zncc(block_sum(pb, q), muA, vb[vo].x, vb[vo].y);
             }
         }
         const unsigned bits = (__ballot_sync(0xffffffffu, direct) >> (16 * h)) & 0x1fu;
@@ -1238,7 +1248,7 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
     const int w = g.w, R = g.R, ND = g.ND;
     const int ng = stencil_groups(g.nwin, w, blockDim.x >> 5);
     const int cp = P.v_pitch;
-    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    const float2 *VV = reinterpret_cast<const float2 *>(Vs);
     const WinOut out = win_out(a, pair);
     const float tau = TAU_PER_PIXEL * (float)(w * w);
     for (int wi = threadIdx.x; wi < g.nwin; wi += blockDim.x) {
@@ -1263,7 +1273,7 @@ static __device__ __forceinline__ void finalize(const PassArgs &a, const TileGeo
                 float num = 0.f;
                 for (int gr = 0; gr < ng; ++gr) num += ws.dpart[(wi * ng + gr) * 5 + p];
                 const int vo = (wyi * g.s + R + 1 + sy) * cp + wxi * g.s + R + 1 + sx;
-                c = scaled_zncc(num, muA, V1[vo], VN[vo]);
+                c = scaled_zncc(num, muA, VV[vo].x, VV[vo].y);
             } else {
                 c = ws.c5[wi * 5 + p];
             }

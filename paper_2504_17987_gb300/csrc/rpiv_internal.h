@@ -77,8 +77,8 @@ struct PassPlan {
     int smem_bytes;
     int off_a, a_pitch;          // A region, floats
     int off_b, b_pitch, padl;    // B' region, floats; logical column 0 at padl - (R+1)
-    int off_h, h_pitch;          // C1 then C2 (column box sums), floats; odd pitch >= BC
-    int off_v, v_pitch;          // V1 (window box sums of B') then VN (1 / sqrt of the box energy), floats; odd pitch >= hw
+    int off_h, h_pitch;          // C: column box sums, (S1, S2) float pairs; odd pitch >= BC, in pairs
+    int off_v, v_pitch;          // V: window box sums, (S1, 1 / sqrt of the box energy) float pairs; odd pitch >= hw, in pairs
     int off_p;                   // block planes (aliases H; a two-row ring of its own in strips)
     int off_tca, tca_pitch;      // 16-bit A copy (TC path; aliases H), elements
     int off_tcb, tcb_pitch;      // two 16-bit B' copies (TC path; aliases H), elements

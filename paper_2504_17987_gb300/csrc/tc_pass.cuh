@@ -467,7 +467,7 @@ static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const float n = (float)(g.w * g.w), tau = TAU_PER_PIXEL * n, nm = n * m;
     const int cp = P.v_pitch;
-    const float *V1 = Vs, *VN = Vs + g.vh * cp;
+    const float2 *VV = reinterpret_cast<const float2 *>(Vs);
     int qv[NQ], vv[NQ];
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
@@ -488,14 +488,14 @@ static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, cons
         }
         const float dmu = muA - m;
         const float *pw = Ps + wi * NP;
-        const float *v1 = V1 + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
-        const float *vn = VN + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
+        const float2 *vb = VV + (wyi * g.s + R + 1) * cp + wxi * g.s + R + 1;
         float best = 0.f;
         uint32_t bq = NONE;
 #pragma unroll
         for (int j = 0; j < NQ; ++j) {
             if (j < NQ - 1 || lane + 32 * j < NP) {
-                const float c = (pw[qv[j]] - dmu * (v1[vv[j]] - nm)) * vn[vv[j]] + 0.f;
+                const float2 bx = vb[vv[j]];
+                const float c = (pw[qv[j]] - dmu * (bx.x - nm)) * bx.y + 0.f;
                 // ascending q: the first of equal values stays; NaN never wins
                 if (c > best || (bq == NONE && c == c)) {
                     best = c;
@@ -520,7 +520,7 @@ static __device__ __forceinline__ void tc_plane_and_peak(const PassArgs &a, cons
             num += q0[rs];
             num += q0[rs + NDN * NDN];
             const int vo = sy * cp + sx;
-            ws.c5[wi * 5 + lane] = scaled_zncc(num, muA, v1[vo], vn[vo]);
+            ws.c5[wi * 5 + lane] = scaled_zncc(num, muA, vb[vo].x, vb[vo].y);
         }
         if (lane == 0) {
             ws.peaks[wi] = bidx;
