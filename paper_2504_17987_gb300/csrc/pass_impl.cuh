@@ -419,30 +419,68 @@ __device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b)
 // thread keeps a running sum over box_lv (columns) or box_lh (rows) outputs;
 // the plan sets them and the number of runs for a full tile, and an edge tile,
 // never larger, skips the runs that start past its end.
-static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
+// split_cols (strips, whose column runs are short: 2R + 3 outputs): one run
+// per column instead, its first w-term sum split between the two half-warps
+// (rows [0, w/2) and [w/2, w)); the lower half-warp then slides down the run.
+// The upper half-warp starts four rows into its range and wraps, so that the
+// two halves' loads fall in different banks (the B' pitch is 4 x odd floats:
+// any two rows w/2 + 4 or 4 apart are 16 banks apart for w/2 a multiple of 8).
+static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs,
+                                                bool split_cols = false)
 {
     const PassPlan &P = a.plan;
     const int w = g.w, tid = threadIdx.x;
     const int cp = P.h_pitch;  // pitch of C in pairs (odd)
     float2 *C = reinterpret_cast<float2 *>(Cs);
-    const int Lv = P.box_lv;
-    for (int it = tid; it < g.BC * P.box_nv; it += blockDim.x) {
-        const int seg = it / g.BC, x = it - seg * g.BC;
-        const int r_lo = seg * Lv, r_hi = min(g.vh, r_lo + Lv);
-        if (r_lo >= g.vh) continue;
-        const float *col = Bs + g.OFFB + x;
-        float s1 = 0.f, s2 = 0.f;
-        for (int y = r_lo; y < r_lo + w; ++y) {
-            const float b = col[y * P.b_pitch];
-            s1 += b;
-            s2 = fmaf(b, b, s2);
+    if (split_cols) {
+        const int lane = tid & 31, hh = lane >> 4, li = lane & 15, half = w >> 1;
+        for (int base = tid - lane; base < 16 * ((g.BC + 15) >> 4) * 2; base += blockDim.x) {
+            const int x0 = (base >> 1) + li, x = min(x0, g.BC - 1);
+            const float *col = Bs + g.OFFB + x;
+            float s1 = 0.f, s2 = 0.f;
+            for (int t = 0; t < half; ++t) {
+                int y = t;
+                if (hh) {
+                    y = t + 4;
+                    if (y >= half) y -= half;
+                    y += half;
+                }
+                const float b = col[y * P.b_pitch];
+                s1 += b;
+                s2 = fmaf(b, b, s2);
+            }
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+            if (hh == 0 && x0 < g.BC) {
+                C[x] = make_float2(s1, s2);
+                for (int r = 1; r < g.vh; ++r) {
+                    const float bo = col[(r - 1) * P.b_pitch], bi = col[(r + w - 1) * P.b_pitch];
+                    s1 += bi - bo;
+                    s2 += bi * bi - bo * bo;
+                    C[r * cp + x] = make_float2(s1, s2);
+                }
+            }
         }
-        C[r_lo * cp + x] = make_float2(s1, s2);
-        for (int r = r_lo + 1; r < r_hi; ++r) {
-            const float bo = col[(r - 1) * P.b_pitch], bi = col[(r + w - 1) * P.b_pitch];
-            s1 += bi - bo;
-            s2 += bi * bi - bo * bo;
-            C[r * cp + x] = make_float2(s1, s2);
+    } else {
+        const int Lv = P.box_lv;
+        for (int it = tid; it < g.BC * P.box_nv; it += blockDim.x) {
+            const int seg = it / g.BC, x = it - seg * g.BC;
+            const int r_lo = seg * Lv, r_hi = min(g.vh, r_lo + Lv);
+            if (r_lo >= g.vh) continue;
+            const float *col = Bs + g.OFFB + x;
+            float s1 = 0.f, s2 = 0.f;
+            for (int y = r_lo; y < r_lo + w; ++y) {
+                const float b = col[y * P.b_pitch];
+                s1 += b;
+                s2 = fmaf(b, b, s2);
+            }
+            C[r_lo * cp + x] = make_float2(s1, s2);
+            for (int r = r_lo + 1; r < r_hi; ++r) {
+                const float bo = col[(r - 1) * P.b_pitch], bi = col[(r + w - 1) * P.b_pitch];
+                s1 += bi - bo;
+                s2 += bi * bi - bo * bo;
+                C[r * cp + x] = make_float2(s1, s2);
+            }
         }
     }
     __syncthreads();
@@ -471,18 +509,27 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
 // bst[b] = (sum, M2).  For G a power of two from 4 to 32 one thread takes a
 // block row (128-bit loads) and the G rows of a block, in aligned lanes of one
 // warp, are summed by shuffles; the mean is exact scaling by 1 / G^2.
-static __device__ __forceinline__ void block_stats_rows(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
+// b0: first block (a strip step after its first computes only the block row
+// it adds); ring_wy >= 0: strip mode, block row by of window row ring_wy is
+// kept in ring row (ring_wy + by) & 1, as the planes are.
+__device__ __forceinline__ int block_slot(const TileGeom &g, int byi, int bxi, int ring_wy)
+{
+    return ring_wy < 0 ? byi * g.nbx + bxi : ((ring_wy + byi) & 1) * g.nbx + bxi;
+}
+
+static __device__ __forceinline__ void block_stats_rows(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst,
+                                                        int b0, int ring_wy)
 {
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31;
     const int G = g.G, lg = __ffs(G) - 1;
     const float inv_n = 1.f / (float)(G * G);
-    const int items = g.nb * G;
+    const int items = (g.nb - b0) * G;
     // warp-uniform trip count: every lane takes part in the shuffles; lanes
     // past the end repeat the last row and store nothing
     for (int base = threadIdx.x - lane; base < items; base += blockDim.x) {
         const int it = min(base + lane, items - 1);
-        const int b = it >> lg, row = it & (G - 1);
+        const int b = b0 + (it >> lg), row = it & (G - 1);
         const int byi = b / g.nbx, bxi = b - byi * g.nbx;
         const float *p = As + (byi * G + row) * P.a_pitch + bxi * G;
         float s = 0.f;
@@ -504,22 +551,23 @@ static __device__ __forceinline__ void block_stats_rows(const PassArgs &a, const
             q = fmaf(v.w - m, v.w - m, q);
         }
         for (int o = 1; o < G; o <<= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        if (base + lane < items && row == 0) bst[b] = make_float2(s, q);
+        if (base + lane < items && row == 0) bst[block_slot(g, byi, bxi, ring_wy)] = make_float2(s, q);
     }
 }
 
 // Any G: one warp per block, lanes along the rows.
-static __device__ __forceinline__ void block_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst)
+static __device__ __forceinline__ void block_stats(const PassArgs &a, const TileGeom &g, const float *As, float2 *bst,
+                                                   int b0 = 0, int ring_wy = -1)
 {
     if (g.G >= 4 && g.G <= 32 && (g.G & (g.G - 1)) == 0) {
-        block_stats_rows(a, g, As, bst);
+        block_stats_rows(a, g, As, bst, b0, ring_wy);
         return;
     }
     const PassPlan &P = a.plan;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int G = g.G;
     const float n = (float)(G * G);
-    for (int b = warp; b < g.nb; b += nwarps) {
+    for (int b = b0 + warp; b < g.nb; b += nwarps) {
         const int bxi = b % g.nbx, byi = b / g.nbx;
         const float *base = As + (byi * G) * P.a_pitch + bxi * G;
         float s = 0.f;
@@ -532,13 +580,14 @@ static __device__ __forceinline__ void block_stats(const PassArgs &a, const Tile
             q = fmaf(d, d, q);
         }
         q = warp_sum(q);
-        if (lane == 0) bst[b] = make_float2(s, q);
+        if (lane == 0) bst[block_slot(g, byi, bxi, ring_wy)] = make_float2(s, q);
     }
 }
 
 // Window mean and energy from its blocks (parallel-variance identity):
 // E = sum M2_b + n_b sum (mean_b - mean)^2, in a fixed order.
-static __device__ __forceinline__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *bst, float *stats)
+static __device__ __forceinline__ void window_stats(const PassArgs &a, const TileGeom &g, const float2 *bst, float *stats,
+                                                    int ring_wy = -1)
 {
     (void)a;
     const int G = g.G, kb = g.w / G;
@@ -548,12 +597,12 @@ static __device__ __forceinline__ void window_stats(const PassArgs &a, const Til
         const int bx0 = (wxi * g.s) / G, by0 = (wyi * g.s) / G;
         float s = 0.f;
         for (int yy = 0; yy < kb; ++yy)
-            for (int xx = 0; xx < kb; ++xx) s += bst[(by0 + yy) * g.nbx + bx0 + xx].x;
+            for (int xx = 0; xx < kb; ++xx) s += bst[block_slot(g, by0 + yy, bx0 + xx, ring_wy)].x;
         const float mean = s / n;
         float e = 0.f;
         for (int yy = 0; yy < kb; ++yy)
             for (int xx = 0; xx < kb; ++xx) {
-                const float2 p = bst[(by0 + yy) * g.nbx + bx0 + xx];
+                const float2 p = bst[block_slot(g, by0 + yy, bx0 + xx, ring_wy)];
                 const float d = p.x / nb - mean;
                 e += p.y + nb * d * d;
             }
@@ -1496,10 +1545,10 @@ __global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(c
             return;
         }
         // 2: statistics and box sums of the row
-        block_stats(a, g, As, bst);
-        box_sums(a, g, Bs, Cs, Vs);  // contains a barrier between its two passes
+        block_stats(a, g, As, bst, k == 0 ? 0 : g.nbx, wy);
+        box_sums(a, g, Bs, Cs, Vs, true);  // contains a barrier between its two passes
         __syncthreads();
-        window_stats(a, g, bst, stats);
+        window_stats(a, g, bst, stats, wy);
         // 3: planes of the block row this step adds
         block_planes_fp32<RC>(a, g, As, Bs, Ps, k == 0 ? 0 : g.nbx, wy);
         __syncthreads();
