@@ -37,7 +37,8 @@ __device__ __forceinline__ void sort8(float (&v)[8])
     cswap(v[1], v[2]); cswap(v[3], v[4]); cswap(v[5], v[6]);
 }
 
-// Median of the first c entries (c in 1..8) of v; the rest must be +inf.
+// Median of the first c entries (c in 1..8) of v once sorted; the rest must
+// be +inf.  v is left sorted.
 __device__ __forceinline__ float median_sorted(float (&v)[8], int c)
 {
     sort8(v);
@@ -85,46 +86,33 @@ __global__ void __launch_bounds__(256) uod_kernel(const UodArgs a)
         unsigned char bad = 0;
         if (sok[jj][ii]) {
             if (info && !(info[j * a.nx + i] & 1)) bad = 1;
+            // the neighbours in a fixed order, +inf where a node is missing:
+            // sorting puts the c present values first, in the same order as
+            // any packing of them would
             float nu[8], nv[8];
-            int c = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                nu[q] = INFINITY;
-                nv[q] = INFINITY;
-            }
+            int c = 0, q = 0;
 #pragma unroll
             for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
                 for (int di = -1; di <= 1; ++di) {
                     if (di == 0 && dj == 0) continue;
-                    if (sok[jj + dj][ii + di]) {
-                        // c < 8 always holds here
-#pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            if (q == c) {
-                                nu[q] = su[jj + dj][ii + di];
-                                nv[q] = sv[jj + dj][ii + di];
-                            }
-                        ++c;
-                    }
+                    const bool ok = sok[jj + dj][ii + di];
+                    nu[q] = ok ? su[jj + dj][ii + di] : INFINITY;
+                    nv[q] = ok ? sv[jj + dj][ii + di] : INFINITY;
+                    c += ok ? 1 : 0;
+                    ++q;
                 }
             if (c > 0) {
-                float tu[8], tv[8];
+                // nu, nv sorted in place: the residuals of their first c entries
+                const float um = median_sorted(nu, c);
+                const float vm = median_sorted(nv, c);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    tu[q] = nu[q];
-                    tv[q] = nv[q];
+                for (int q2 = 0; q2 < 8; ++q2) {
+                    nu[q2] = q2 < c ? fabsf(nu[q2] - um) : INFINITY;
+                    nv[q2] = q2 < c ? fabsf(nv[q2] - vm) : INFINITY;
                 }
-                const float um = median_sorted(tu, c);
-                const float vm = median_sorted(tv, c);
-                float ru[8], rv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    ru[q] = q < c ? fabsf(nu[q] - um) : INFINITY;
-                    rv[q] = q < c ? fabsf(nv[q] - vm) : INFINITY;
-                }
-                const float rmu = median_sorted(ru, c);
-                const float rmv = median_sorted(rv, c);
+                const float rmu = median_sorted(nu, c);
+                const float rmv = median_sorted(nv, c);
                 const float r0u = fabsf(su[jj][ii] - um) / (rmu + a.eps);
                 const float r0v = fabsf(sv[jj][ii] - vm) / (rmv + a.eps);
                 if (r0u > a.thr || r0v > a.thr) bad = 1;
@@ -145,26 +133,17 @@ __global__ void __launch_bounds__(256) uod_kernel(const UodArgs a)
             const bool bad = sbad[jj - 1][ii - 1];
             if (bad && a.replace) {
                 float nu[8], nv[8];
-                int c = 0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    nu[q] = INFINITY;
-                    nv[q] = INFINITY;
-                }
+                int c = 0, q = 0;
 #pragma unroll
                 for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
                     for (int di = -1; di <= 1; ++di) {
                         if (di == 0 && dj == 0) continue;
-                        if (sok[jj + dj][ii + di] && !sbad[jj + dj - 1][ii + di - 1]) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q)
-                                if (q == c) {
-                                    nu[q] = su[jj + dj][ii + di];
-                                    nv[q] = sv[jj + dj][ii + di];
-                                }
-                            ++c;
-                        }
+                        const bool ok = sok[jj + dj][ii + di] && !sbad[jj + dj - 1][ii + di - 1];
+                        nu[q] = ok ? su[jj + dj][ii + di] : INFINITY;
+                        nv[q] = ok ? sv[jj + dj][ii + di] : INFINITY;
+                        c += ok ? 1 : 0;
+                        ++q;
                     }
                 if (c > 0) {
                     ru = median_sorted(nu, c);
@@ -313,19 +292,72 @@ __device__ __forceinline__ float box2(const unsigned char *img, long long pitch,
                     (ldp<T>(img, pitch, 2 * x, 2 * y + 1) + ldp<T>(img, pitch, 2 * x + 1, 2 * y + 1)));
 }
 
-__global__ void down_kernel(const DownArgs a)
+// Eight consecutive source pixels of a row from pixel p (p a multiple of 8):
+// one 8-byte (u8), 16-byte (u16) or two 16-byte (float) loads.
+template <typename T>
+__device__ __forceinline__ void load8(const unsigned char *row, int p, float (&v)[8])
+{
+    if (sizeof(T) == 1) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row) + p / 8);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[i] = (float)((u.x >> (8 * i)) & 0xffu);
+            v[4 + i] = (float)((u.y >> (8 * i)) & 0xffu);
+        }
+    } else if (sizeof(T) == 2) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(row) + p / 8);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[2 * i] = (float)(w[i] & 0xffffu);
+            v[2 * i + 1] = (float)(w[i] >> 16);
+        }
+    } else {
+        const float4 f0 = __ldg(reinterpret_cast<const float4 *>(row) + p / 4);
+        const float4 f1 = __ldg(reinterpret_cast<const float4 *>(row) + p / 4 + 1);
+        v[0] = f0.x; v[1] = f0.y; v[2] = f0.z; v[3] = f0.w;
+        v[4] = f1.x; v[5] = f1.y; v[6] = f1.z; v[7] = f1.w;
+    }
+}
+
+// Four consecutive outputs per thread (x0 = 4 k): their 2 x 8 source pixels by
+// one vector load per source row and one 16-byte store, where the source rows
+// and the destination row are aligned for them (checked per pair); the row's
+// last outputs and unaligned rows take the scalar form.  Same sums, in the
+// same order, either way.
+template <typename T>
+__device__ __forceinline__ void down_row4(const unsigned char *src, long long pitch, int x0, int y, int W2, float *d,
+                                          bool vec)
+{
+    if (vec && x0 + 4 <= W2) {
+        float r0[8], r1[8];
+        load8<T>(src + (long long)(2 * y) * pitch, 2 * x0, r0);
+        load8<T>(src + (long long)(2 * y + 1) * pitch, 2 * x0, r1);
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = 0.25f * ((r0[2 * i] + r0[2 * i + 1]) + (r1[2 * i] + r1[2 * i + 1]));
+        *reinterpret_cast<float4 *>(d) = make_float4(o[0], o[1], o[2], o[3]);
+        return;
+    }
+    for (int k = 0; k < 4 && x0 + k < W2; ++k) d[k] = box2<T>(src, pitch, x0 + k, y);
+}
+
+__global__ void __launch_bounds__(256) down_kernel(const DownArgs a)
 {
     const int pair = blockIdx.z;
     const int W2 = a.W / 2, H2 = a.H / 2;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W2 || y >= H2) return;
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= W2 || y >= H2) return;
     const unsigned char *src = (const unsigned char *)resolve(a.src, pair);
     float *dst = (float *)resolve(a.dst, pair);
-    float val;
-    if (a.fmt == PIX_U8) val = box2<uint8_t>(src, a.pitch, x, y);
-    else if (a.fmt == PIX_U16) val = box2<uint16_t>(src, a.pitch, x, y);
-    else val = box2<float>(src, a.pitch, x, y);
-    dst[(long long)(y + a.dst_margin) * a.dst_pitch + (x + a.dst_margin)] = val;
+    float *d = dst + (long long)(y + a.dst_margin) * a.dst_pitch + (x0 + a.dst_margin);
+    const int bpp = a.fmt == PIX_U8 ? 1 : (a.fmt == PIX_U16 ? 2 : 4);
+    const int align = bpp == 1 ? 8 : 16;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)a.pitch) % align) == 0 &&
+                     (reinterpret_cast<uintptr_t>(d) % 16) == 0;
+    if (a.fmt == PIX_U8) down_row4<uint8_t>(src, a.pitch, x0, y, W2, d, vec);
+    else if (a.fmt == PIX_U16) down_row4<uint16_t>(src, a.pitch, x0, y, W2, d, vec);
+    else down_row4<float>(src, a.pitch, x0, y, W2, d, vec);
 }
 
 // Four consecutive pixels per thread: one 4-, 8- or 16-byte load and one
@@ -406,12 +438,17 @@ cudaError_t launch_ingest(const IngestArgs &a, int n_pairs, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// 256 threads per CTA: up to 128 along a row (four outputs each), the rest
+// over rows
 cudaError_t launch_down(const DownArgs &a, int n_pairs, cudaStream_t st)
 {
     const int W2 = a.W / 2, H2 = a.H / 2;
     if (W2 < 1 || H2 < 1) return cudaSuccess;
-    dim3 grid((W2 + 255) / 256, H2, n_pairs);
-    down_kernel<<<grid, 256, 0, st>>>(a);
+    const int quads = (W2 + 3) / 4;
+    const int tx = std::min(128, (quads + 31) / 32 * 32), ty = 256 / tx;
+    dim3 block(tx, ty);
+    dim3 grid((quads + tx - 1) / tx, (H2 + ty - 1) / ty, n_pairs);
+    down_kernel<<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -123,18 +123,23 @@ def check_16bit_pass(r, R, precision, tie_tol=0.02):
 # ----------------------------------------------------------------- stages ---
 
 @pytest.mark.parametrize("kind", ["u8", "u16", "f32"])
-def test_downsample_bit_exact(kind):
+@pytest.mark.parametrize("H, W, Wp", [(91, 130, 130), (37, 270, 272), (40, 256, 256)])
+def test_downsample_bit_exact(kind, H, W, Wp):
+    """2x2 box level against the oracle, bit for bit: odd sizes (last row and
+    column dropped), unaligned rows (scalar loads), and rows aligned for the
+    kernel's vector loads with a ragged end of row (W / 2 not a multiple of 4)
+    and output rows of mixed alignment (W / 2 = 135 floats apart)."""
     rng = np.random.default_rng(1)
-    H, W = 91, 130  # odd sizes: last row dropped
     if kind == "u8":
-        img = rng.integers(0, 256, (H, W)).astype(np.uint8)
+        img = rng.integers(0, 256, (H, Wp)).astype(np.uint8)
     elif kind == "u16":
-        img = rng.integers(0, 4096, (H, W)).astype(np.uint16)
+        img = rng.integers(0, 4096, (H, Wp)).astype(np.uint16)
     else:
-        img = (rng.integers(0, 4096 * 4, (H, W)) / 4.0).astype(np.float32)
+        img = (rng.integers(0, 4096 * 4, (H, Wp)) / 4.0).astype(np.float32)
     t = dev(img) if kind != "f32" else torch.from_numpy(img).cuda()
+    t = t[:, :W]  # rows Wp pixels apart
     out = rp.stage_downsample(t).cpu().numpy()
-    ref = oracle.downsample(img.astype(np.float64))
+    ref = oracle.downsample(img[:, :W].astype(np.float64))
     assert out.shape == ref.shape
     assert np.array_equal(out.astype(np.float64), ref)
 
