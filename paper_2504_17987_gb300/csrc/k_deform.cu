@@ -24,8 +24,12 @@ namespace {
 // (the per-tile set-up is spread over more pixels), 64 x 64 otherwise.
 constexpr int DTX = 64, DTY_MAX = 128;
 constexpr int DROWS = 8;            // rows per thread and 32-row slice (256 threads = 64 columns x 4 row phases)
-constexpr int NODE_CAP = 1152;      // nodes a tile can touch (checked on the host; steps >= 3)
-constexpr int nrow_cap(int dty) { return dty / 3 + 4; }  // node rows a tile touches (steps >= 3, checked on the host)
+// Nodes and node rows a tile can touch, for steps >= 3 and for steps >= 8
+// (checked on the host).  The shared arrays are sized by these caps: the
+// smaller ones leave more of the SM's combined L1 / shared memory to the L1
+// that serves the gathers.
+constexpr int NODE_CAP = 1152, NODE_CAP_S8 = 256;
+constexpr int nrow_cap(int dty, int min_step) { return dty / min_step + 4; }
 
 // cell index and weight of a pixel position along one axis of the node grid
 // (node i at c0 + i s; positions outside the hull take the border value)
@@ -155,12 +159,13 @@ __device__ __forceinline__ void deform_rows_any(const DeformArgs &a, const T *ba
 // one interpolation along y.  A tile whose taps provably stay inside the image
 // (its displacement lies within the range of its nodes, a convex combination)
 // skips the clamping; either way every tap is the clamp-to-edge sample.
-template <typename T, int DTY>
+template <typename T, int DTY, int MIN_STEP>
 __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const float *pu, const float *pv,
                             float *out)
 {
-    __shared__ float nu[NODE_CAP], nv[NODE_CAP];
-    __shared__ float2 cuv[nrow_cap(DTY) * DTX];
+    constexpr int NCAP = MIN_STEP >= 8 ? NODE_CAP_S8 : NODE_CAP;
+    __shared__ float nu[NCAP], nv[NCAP];
+    __shared__ float2 cuv[nrow_cap(DTY, MIN_STEP) * DTX];
     __shared__ int2 rinfo[DTY];
     __shared__ float red[4][8];
     const int x0 = blockIdx.x * DTX - a.M, y0 = blockIdx.y * DTY - a.M;
@@ -262,16 +267,26 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
 }
 
 // one kernel per pixel type, so that each holds a single copy of the tile's
-// shared arrays
-template <typename T, int DTY>
-__global__ void __launch_bounds__(256) deform_kernel(const DeformArgs a)
+// shared arrays; MIN_STEP: the smallest node step its caps allow (3 or 8).
+// Six CTAs per SM (40 registers).
+template <typename T, int DTY, int MIN_STEP>
+__global__ void __launch_bounds__(256, 6) deform_kernel(const DeformArgs a)
 {
     const int pair = blockIdx.z;
     const unsigned char *img = (const unsigned char *)resolve(a.img, pair);
     const float *pu = (const float *)resolve(a.pred_u, pair);
     const float *pv = (const float *)resolve(a.pred_v, pair);
     float *out = (float *)resolve(a.out, pair);
-    deform_tile<T, DTY>(a, img, pu, pv, out);
+    deform_tile<T, DTY, MIN_STEP>(a, img, pu, pv, out);
+}
+
+// nodes touched by a DTX x dty tile along each axis, plus the neighbour node,
+// within the caps of the kernel for steps >= min_step
+bool nodes_fit(int s, int nx, int ny, int dty, int min_step)
+{
+    const int cx = DTX / s + 3, cy = dty / s + 3;
+    const int cap = min_step >= 8 ? NODE_CAP_S8 : NODE_CAP;
+    return std::min(cx, nx) * std::min(cy, ny) <= cap && std::min(cy, ny) <= nrow_cap(dty, min_step);
 }
 
 }  // namespace
@@ -279,19 +294,27 @@ __global__ void __launch_bounds__(256) deform_kernel(const DeformArgs a)
 bool deform_nodes_fit(int w, int s, int nx, int ny)
 {
     (void)w;
-    // nodes touched by a DTX x DTY tile along each axis, plus the neighbour node
-    const int cx = DTX / s + 3, cy = DTY_MAX / s + 3;
-    return std::min(cx, nx) * std::min(cy, ny) <= NODE_CAP && std::min(cy, ny) <= nrow_cap(DTY_MAX);
+    return nodes_fit(s, nx, ny, DTY_MAX, 3);
 }
 
-template <int DTY>
-static void launch_tiles(const DeformArgs &a, int n_pairs, cudaStream_t st)
+template <int DTY, int MIN_STEP>
+static void launch_tiles_caps(const DeformArgs &a, int n_pairs, cudaStream_t st)
 {
     const int WE = a.W + 2 * a.M, HE = a.H + 2 * a.M;
     dim3 grid((WE + DTX - 1) / DTX, (HE + DTY - 1) / DTY, n_pairs);
-    if (a.fmt == PIX_U8) deform_kernel<uint8_t, DTY><<<grid, 256, 0, st>>>(a);
-    else if (a.fmt == PIX_U16) deform_kernel<uint16_t, DTY><<<grid, 256, 0, st>>>(a);
-    else deform_kernel<float, DTY><<<grid, 256, 0, st>>>(a);
+    if (a.fmt == PIX_U8) deform_kernel<uint8_t, DTY, MIN_STEP><<<grid, 256, 0, st>>>(a);
+    else if (a.fmt == PIX_U16) deform_kernel<uint16_t, DTY, MIN_STEP><<<grid, 256, 0, st>>>(a);
+    else deform_kernel<float, DTY, MIN_STEP><<<grid, 256, 0, st>>>(a);
+}
+
+// the small-cap kernel whenever the grid fits its caps (no predictor: one
+// zero node row)
+template <int DTY>
+static void launch_tiles(const DeformArgs &a, int n_pairs, cudaStream_t st)
+{
+    const bool has = a.pred_u.base != nullptr && a.pred_v.base != nullptr;
+    if (!has || nodes_fit(a.s, a.nx, a.ny, DTY, 8)) launch_tiles_caps<DTY, 8>(a, n_pairs, st);
+    else launch_tiles_caps<DTY, 3>(a, n_pairs, st);
 }
 
 // 64 x 128 tiles when they still make two full waves (five CTAs per SM on
