@@ -23,7 +23,8 @@ namespace {
 // A tile is DTX x DTY output pixels: 64 x 128 when the batch fills the GPU
 // (the per-tile set-up is spread over more pixels), 64 x 64 otherwise.
 constexpr int DTX = 64, DTY_MAX = 128;
-constexpr int DROWS = 8;            // rows per thread and 32-row slice (256 threads = 64 columns x 4 row phases)
+constexpr int DROWS = 4;            // rows per thread and slice (256 threads = 64 columns x 4 row phases)
+constexpr int SLICE = 4 * DROWS;    // rows per slice
 // Nodes and node rows a tile can touch, for steps >= 3 and for steps >= 8
 // (checked on the host).  The shared arrays are sized by these caps: the
 // smaller ones leave more of the SM's combined L1 / shared memory to the L1
@@ -78,7 +79,7 @@ __device__ __forceinline__ void floor_split(float d, float &fl, int &i)
     i = __float_as_int(fl + 12582912.f) - 0x4B400000;
 }
 
-// The tile in slices of 32 rows; within a slice all rows of a thread are
+// The tile in slices of SLICE rows; within a slice all rows of a thread are
 // unrolled so that their gathers are in flight together; rows and columns
 // past the grown image are computed on clamped coordinates and not stored.
 // CLAMP: the taps are clamped to the image (tiles near its border or with a
@@ -88,15 +89,15 @@ template <int DTY, typename T, typename Off, bool CLAMP>
 __device__ __forceinline__ void deform_rows(const DeformArgs &a, const T *base, float *out, int djo, Off pe, int x,
                                             int y0, int lx, int ly0, const float2 *cuv, const int2 *rinfo)
 {
-    // warps whose 32 columns, and slices whose 32 rows, lie past the grown
+    // warps whose 32 columns, and slices whose rows, lie past the grown
     // image store nothing: skip them (uniform per warp)
     if (x - (int)(threadIdx.x & 31) >= a.W + a.M) return;
-    for (int half = 0; half < DTY / 32; ++half) {
-        if (y0 + 32 * half >= a.H + a.M) break;
+    for (int half = 0; half < DTY / SLICE; ++half) {
+        if (y0 + SLICE * half >= a.H + a.M) break;
         float res[DROWS];
 #pragma unroll
         for (int k = 0; k < DROWS; ++k) {
-            const int ly = 32 * half + ly0 + 4 * k, y = y0 + ly;
+            const int ly = SLICE * half + ly0 + 4 * k, y = y0 + ly;
             const int2 ri = rinfo[ly];
             const float ty = __int_as_float(ri.y);
             const float2 n0 = cuv[ri.x + lx], n1 = cuv[ri.x + djo + lx];
@@ -132,10 +133,10 @@ __device__ __forceinline__ void deform_rows(const DeformArgs &a, const T *base, 
             res[k] = top + tyy * (bot - top);
         }
         if (x < a.W + a.M) {
-            float *o = out + (long long)(y0 + 32 * half + ly0 + a.M) * a.out_pitch + (x + a.M);
+            float *o = out + (long long)(y0 + SLICE * half + ly0 + a.M) * a.out_pitch + (x + a.M);
 #pragma unroll
             for (int k = 0; k < DROWS; ++k) {
-                const int y = y0 + 32 * half + ly0 + 4 * k;
+                const int y = y0 + SLICE * half + ly0 + 4 * k;
                 if (y < a.H + a.M) o[(long long)(4 * k) * a.out_pitch] = res[k];
             }
         }
@@ -270,7 +271,7 @@ __device__ void deform_tile(const DeformArgs &a, const unsigned char *img, const
 // shared arrays; MIN_STEP: the smallest node step its caps allow (3 or 8).
 // Six CTAs per SM (40 registers).
 template <typename T, int DTY, int MIN_STEP>
-__global__ void __launch_bounds__(256, 6) deform_kernel(const DeformArgs a)
+__global__ void __launch_bounds__(256, 8) deform_kernel(const DeformArgs a)
 {
     const int pair = blockIdx.z;
     const unsigned char *img = (const unsigned char *)resolve(a.img, pair);

@@ -42,6 +42,7 @@ __device__ __forceinline__ void sort8(float (&v)[8])
 __device__ __forceinline__ float median_sorted(float (&v)[8], int c)
 {
     sort8(v);
+    if (c == 8) return 0.5f * (v[3] + v[4]);  // every neighbour present: the usual case
     float m = v[0];
 #pragma unroll
     for (int q = 1; q < 8; ++q)
