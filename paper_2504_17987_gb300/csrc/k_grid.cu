@@ -361,43 +361,38 @@ __global__ void __launch_bounds__(256) down_kernel(const DownArgs a)
     else down_row4<float>(src, a.pitch, x0, y, W2, d, vec);
 }
 
-// Four consecutive pixels per thread: one 4-, 8- or 16-byte load and one
-// 16-byte store where the source row and the destination are aligned for it
-// (checked per pair on the device), scalar accesses otherwise.
+// Eight consecutive pixels per thread: one 8-byte (u8), 16-byte (u16) or two
+// 16-byte (float) loads and two 16-byte stores where the source row and the
+// destination are aligned for them (checked per pair on the device), scalar
+// accesses otherwise.
 template <typename T>
-__device__ __forceinline__ void ingest_row4(const unsigned char *row, int x, int W, float *d, bool vec)
+__device__ __forceinline__ void ingest_row8(const unsigned char *row, int x, int W, float *d, bool vec)
 {
-    if (vec && x + 4 <= W) {
-        float4 o;
-        if (sizeof(T) == 1) {
-            const uchar4 v = __ldg(reinterpret_cast<const uchar4 *>(row) + x / 4);
-            o = make_float4(v.x, v.y, v.z, v.w);
-        } else if (sizeof(T) == 2) {
-            const ushort4 v = __ldg(reinterpret_cast<const ushort4 *>(row) + x / 4);
-            o = make_float4(v.x, v.y, v.z, v.w);
-        } else {
-            o = __ldg(reinterpret_cast<const float4 *>(row) + x / 4);
-        }
-        *reinterpret_cast<float4 *>(d) = o;
+    if (vec && x + 8 <= W) {
+        float v[8];
+        load8<T>(row, x, v);
+        *reinterpret_cast<float4 *>(d) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(d + 4) = make_float4(v[4], v[5], v[6], v[7]);
         return;
     }
-    for (int k = 0; k < 4 && x + k < W; ++k) d[k] = (float)__ldg(reinterpret_cast<const T *>(row) + x + k);
+    for (int k = 0; k < 8 && x + k < W; ++k) d[k] = (float)__ldg(reinterpret_cast<const T *>(row) + x + k);
 }
 
 __global__ void ingest_kernel(const IngestArgs a)
 {
     const int pair = blockIdx.z;
-    const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y;
+    const int x = 8 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y;
     if (x >= a.W) return;
     const unsigned char *src = (const unsigned char *)resolve(a.src, pair);
     float *dst = (float *)resolve(a.dst, pair);
     const int bpp = a.fmt == PIX_U8 ? 1 : (a.fmt == PIX_U16 ? 2 : 4);
     const unsigned char *row = src + (long long)y * a.pitch;
     float *d = dst + (long long)(y + a.dst_margin) * a.dst_pitch + (x + a.dst_margin);
-    const bool vec = ((reinterpret_cast<uintptr_t>(row) % (4 * bpp)) == 0) && ((reinterpret_cast<uintptr_t>(d) % 16) == 0);
-    if (a.fmt == PIX_U8) ingest_row4<uint8_t>(row, x, a.W, d, vec);
-    else if (a.fmt == PIX_U16) ingest_row4<uint16_t>(row, x, a.W, d, vec);
-    else ingest_row4<float>(row, x, a.W, d, vec);
+    const uintptr_t align = bpp == 1 ? 8 : 16;
+    const bool vec = ((reinterpret_cast<uintptr_t>(row) % align) == 0) && ((reinterpret_cast<uintptr_t>(d) % 16) == 0);
+    if (a.fmt == PIX_U8) ingest_row8<uint8_t>(row, x, a.W, d, vec);
+    else if (a.fmt == PIX_U16) ingest_row8<uint16_t>(row, x, a.W, d, vec);
+    else ingest_row8<float>(row, x, a.W, d, vec);
 }
 
 // One CTA copies UPLOAD_ROWS rows of one frame of one pair: 16-byte words
@@ -434,7 +429,7 @@ cudaError_t launch_upload(const UploadArgs &a, int n_pairs, cudaStream_t st)
 
 cudaError_t launch_ingest(const IngestArgs &a, int n_pairs, cudaStream_t st)
 {
-    dim3 grid((a.W + 4 * 128 - 1) / (4 * 128), a.H, n_pairs);
+    dim3 grid((a.W + 8 * 128 - 1) / (8 * 128), a.H, n_pairs);
     ingest_kernel<<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
