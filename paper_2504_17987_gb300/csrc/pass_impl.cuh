@@ -1037,9 +1037,10 @@ struct WinShared {
 // (q = lane + 32 j) once, into plane and box-sum offsets kept in registers.
 // ONE_PLANE: one plane per block (FP32 planes), so the block stride is NP.
 // ring_wy >= 0: strip mode, the window's block rows yy sit in ring rows
-// (ring_wy + yy) & 1.
+// (ring_wy + yy) & 1.  Returns whether this thread stored a nonzero
+// direct-sum mask (some window needs the direct stencil).
 template <int RC, bool ONE_PLANE>
-static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
+static __device__ __forceinline__ bool plane_and_peak(const PassArgs &a, const TileGeom &g, const float *Ps, const float *Vs,
                                       const float *stats, bool tc, const WinShared &ws, int ring_wy = -1,
                                       float moff = 0.f)
 {
@@ -1079,6 +1080,7 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
     auto coef = [&](float num, float muA, float S1, float nB) {
         return tc ? (num - (muA - moff) * (S1 - nm)) * nB + 0.f : scaled_zncc(num, muA, S1, nB);
     };
+    bool any_need = false;
     for (Walk2D wk(warp, nwarps, g.nwx); wk.y < g.nwy; wk.next()) {
         const int wxi = wk.x, wyi = wk.y, wi = wyi * g.nwx + wxi;
         const float muA = stats[2 * wi], EA = stats[2 * wi + 1];
@@ -1132,9 +1134,11 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
             if (lane == 0) {
                 ws.peaks[wi] = bidx;
                 ws.need[wi] = (int)bits;
+                any_need |= bits != 0u;
             }
         }
     }
+    return any_need;
 }
 
 // FP32 planes, compile-time radius: two windows per warp, one per half-warp
@@ -1144,7 +1148,7 @@ static __device__ __forceinline__ void plane_and_peak(const PassArgs &a, const T
 // value, ties to the smallest row-major index, NaN never winning.  Results
 // as plane_and_peak.
 template <int RC>
-static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, const TileGeom &g, const float *Ps,
+static __device__ __forceinline__ bool plane_and_peak_pairs(const PassArgs &a, const TileGeom &g, const float *Ps,
                                             const float *Vs, const float *stats, const WinShared &ws,
                                             int ring_wy = -1)
 {
@@ -1176,6 +1180,7 @@ static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, c
         return num;
     };
     const int npairs = (g.nwin + 1) >> 1;
+    bool any_need = false;
     for (int pw = warp; pw < npairs; pw += nwarps) {
         const int wi = 2 * pw + h;
         const bool has = wi < g.nwin;  // the second half of an odd tile's last pair idles
@@ -1227,8 +1232,10 @@ static __device__ __forceinline__ void plane_and_peak_pairs(const PassArgs &a, c
         if (has && hl == 0) {
             ws.peaks[wi] = live ? bidx : NP / 2;
             ws.need[wi] = live ? (int)bits : 0;
+            any_need |= live && bits != 0u;
         }
     }
+    return any_need;
 }
 
 // Row groups per window in the direct stencil: enough (window, group) items
@@ -1466,13 +1473,17 @@ __global__ void __launch_bounds__(PASS_THREADS,
     // two windows per warp once the tile has at least two per warp (16 px
     // tiles: 1.207 -> 1.198 ms per 64-pair launch; with fewer windows the
     // warps left idle cost more than the shared set-up saves)
+    bool needs;
     if (PREC == PREC_FP32 && RC >= 0 && g.nwin >= 2 * (int)(blockDim.x >> 5))
-        plane_and_peak_pairs<(RC >= 0 ? RC : 0)>(a, g, Ps, Vs, stats, ws);
+        needs = plane_and_peak_pairs<(RC >= 0 ? RC : 0)>(a, g, Ps, Vs, stats, ws);
     else
-        plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws, -1, moff);
-    __syncthreads();
-    stencil_direct(a, g, As, Bs, ws);
-    __syncthreads();
+        needs = plane_and_peak<RC, PREC == PREC_FP32>(a, g, Ps, Vs, stats, tc, ws, -1, moff);
+    // the direct stencil and its barrier only when some window needs them
+    // (peaks at the edge of the search, and every window on the 16-bit path)
+    if (__syncthreads_or(needs)) {
+        stencil_direct(a, g, As, Bs, ws);
+        __syncthreads();
+    }
     finalize(a, g, Vs, stats, ws, pair);
 }
 
@@ -1556,10 +1567,11 @@ __global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(c
         block_planes_fp32<RC>(a, g, As, Bs, Ps, k == 0 ? 0 : g.nbx, wy);
         __syncthreads();
         // 4: plane, argmax, FP32 stencil, Gaussian fit, outputs
-        plane_and_peak<RC, true>(a, g, Ps, Vs, stats, false, ws, wy);
-        __syncthreads();
-        stencil_direct(a, g, As, Bs, ws);
-        __syncthreads();
+        // the direct stencil and its barrier only when some window needs them
+        if (__syncthreads_or(plane_and_peak<RC, true>(a, g, Ps, Vs, stats, false, ws, wy))) {
+            stencil_direct(a, g, As, Bs, ws);
+            __syncthreads();
+        }
         // the regions are read no more in this step: the next step's copies go
         // out now, behind the CTA barrier that ordered the reads, from warp 1,
         // so that they do not wait for the fit that warp 0's first lanes run
