@@ -409,7 +409,8 @@ __device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b)
     return d;
 }
 
-// Window box sums of B' and B'^2 at every shift, in two sliding passes:
+// Window box sums of B' and B'^2 at every shift, in two sliding passes (box_cols, then
+// box_rows once the column sums are visible to the CTA):
 //   C[r][x] = sum_{y=r}^{r+w-1} (B'[y][x], B'[y][x]^2)   (threads along x: conflict free)
 //   V[r][c] = sum_{x=c}^{c+w-1} C[r][x]                  (threads along r, odd pitch)
 // so V[r][c] sums the w x w box whose top-left logical B' pixel is (r, c); its
@@ -425,8 +426,8 @@ __device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b)
 // The upper half-warp starts four rows into its range and wraps, so that the
 // two halves' loads fall in different banks (the B' pitch is 4 x odd floats:
 // any two rows w/2 + 4 or 4 apart are 16 banks apart for w/2 a multiple of 8).
-static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs,
-                                                bool split_cols = false)
+static __device__ __forceinline__ void box_cols(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs,
+                                                bool split_cols)
 {
     const PassPlan &P = a.plan;
     const int w = g.w, tid = threadIdx.x;
@@ -483,7 +484,15 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
             }
         }
     }
-    __syncthreads();
+}
+
+// The row pass of the window box sums, from the column sums C (complete and
+// visible to the CTA).
+static __device__ __forceinline__ void box_rows(const PassArgs &a, const TileGeom &g, const float *Cs, float *Vs)
+{
+    const PassPlan &P = a.plan;
+    const int w = g.w, tid = threadIdx.x;
+    const int cp = P.h_pitch;  // pitch of C in pairs (odd)
     const int vp = P.v_pitch;  // pitch of V in pairs (odd, >= hw)
     const float inv_n = 1.f / (float)(w * w), tau = TAU_PER_PIXEL * (float)(w * w);
     float2 *V = reinterpret_cast<float2 *>(Vs);
@@ -503,6 +512,14 @@ static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeo
             vr[c] = make_float2(lo_f2(s), inv_norm(lo_f2(s), hi_f2(s), inv_n, tau));
         }
     }
+}
+
+// Both passes, with the CTA barrier between them.
+static __device__ __forceinline__ void box_sums(const PassArgs &a, const TileGeom &g, const float *Bs, float *Cs, float *Vs)
+{
+    box_cols(a, g, Bs, Cs, false);
+    __syncthreads();
+    box_rows(a, g, Cs, Vs);
 }
 
 // Sum and centred sum of squares of every G x G block of A (two passes):
@@ -1560,10 +1577,14 @@ __global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(c
         }
         // 2: statistics and box sums of the row
         block_stats(a, g, As, bst, k == 0 ? 0 : g.nbx, wy);
-        box_sums(a, g, Bs, Cs, Vs, true);  // contains a barrier between its two passes
+        box_cols(a, g, Bs, Cs, true);
         __syncthreads();
+        // 3: the row pass of the box sums and the window statistics beside the
+        // planes of the block row this step adds: the planes' ring lies apart
+        // from the column sums, so no barrier separates them (the warps with
+        // row items take their plane items after them)
+        box_rows(a, g, Cs, Vs);
         window_stats(a, g, bst, stats, wy);
-        // 3: planes of the block row this step adds
         block_planes_fp32<RC>(a, g, As, Bs, Ps, k == 0 ? 0 : g.nbx, wy);
         __syncthreads();
         // 4: plane, argmax, FP32 stencil, Gaussian fit, outputs
