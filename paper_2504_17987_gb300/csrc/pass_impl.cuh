@@ -1507,12 +1507,12 @@ __global__ void __launch_bounds__(PASS_THREADS,
 // A strip: one CTA walks P.strip_rows window rows of a one-row tile of TX
 // windows (50 % overlap, blocks of GC px: a window is 2 x 2 blocks).  Each step
 // loads its regions (the rows it shares with the previous step come from L2),
-// recomputes the statistics and box sums, computes the planes of the block row
-// it adds (both block rows on its first step) into a two-row ring, and takes
-// the block row it shares with the previous window row from the ring.  The
+// recomputes the box sums, computes the statistics and the planes of the block
+// row it adds (both block rows on its first step) into two-row rings, and takes
+// the block row it shares with the previous window row from the rings.  The
 // next step's copies are issued once the regions are last read (after the
-// direct stencil), so that they overlap the fit.  GC is a multiple of 4: every
-// region row is one bulk copy.
+// direct stencil, when a window needs it), so that they overlap the fit.  GC is
+// a multiple of 4: every region row is one bulk copy.
 template <int RC, int GC>
 __global__ void __launch_bounds__(PASS_THREADS, GC == 32 ? 3 : 4) strip_kernel(const __grid_constant__ PassArgs a)
 {
