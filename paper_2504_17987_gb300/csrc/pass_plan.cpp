@@ -489,9 +489,15 @@ bool pass_plan(int w, int s, int R, int nx, int ny, int prec, PassPlan *plan, Pa
 }
 
 // A strip launch walks its segments serially inside each CTA, so it is taken
-// only when the batch gives it about four waves of CTAs (three per SM of the
-// device).  RPIV_STRIP_MIN_CTAS overrides the threshold (tuning, and the
-// tests that run both forms); it is read at each launch.
+// only when its segments (8 window rows, or 4 or 2) give at least 1.5 CTAs per
+// SM of the device.  Swept on the 1 MP workload, whose captured batch runs as
+// two halves of 32 pairs on forked streams, and on single pairs: with four
+// waves (1824 CTAs on 152 SMs) the pyramid passes of a half and every pass of
+// a single pair took tiles; at 1.5 per SM they take 8- to 2-row strips,
+// 18,968 -> 19,209 pairs/s and 0.188 -> 0.177 ms per single pair on the device.
+// Fewer CTAs were slower: 100 gave a single pair 4-row strips for the 32 px
+// pass (0.205 ms).  RPIV_STRIP_MIN_CTAS overrides the threshold (tuning, and
+// the tests that run both forms); it is read at each launch.
 long long strip_min_ctas()
 {
     const char *e = std::getenv("RPIV_STRIP_MIN_CTAS");
@@ -499,7 +505,7 @@ long long strip_min_ctas()
         const long long v = std::atoll(e);
         if (v >= 1) return v;
     }
-    return 4LL * device_sm_count() * 3;
+    return 3LL * device_sm_count() / 2;
 }
 
 cudaError_t launch_pass(const PassArgs &args_in, int n_pairs, cudaStream_t st)
