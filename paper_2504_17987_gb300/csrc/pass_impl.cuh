@@ -1161,9 +1161,9 @@ static __device__ __forceinline__ bool plane_and_peak(const PassArgs &a, const T
 // FP32 planes, compile-time radius: two windows per warp, one per half-warp
 // (window 2 pw + h for half h), 16 lanes over the shifts q = lane + 16 j, so
 // that the per-window set-up, reduction and stencil work is shared by two
-// windows.  The half's argmax is a butterfly over (order key, q): the largest
-// value, ties to the smallest row-major index, NaN never winning.  Results
-// as plane_and_peak.
+// windows.  The half's argmax takes two reductions over its 16 lanes (order
+// key, then q): the largest value, ties to the smallest row-major index, NaN
+// never winning.  Results as plane_and_peak.
 template <int RC>
 static __device__ __forceinline__ bool plane_and_peak_pairs(const PassArgs &a, const TileGeom &g, const float *Ps,
                                             const float *Vs, const float *stats, const WinShared &ws,
@@ -1222,15 +1222,13 @@ static __device__ __forceinline__ bool plane_and_peak_pairs(const PassArgs &a, c
                 }
             }
         }
-        uint32_t key = bq == NONE ? 0u : ord_key(best), kq = bq;
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-            const uint32_t ok = __shfl_xor_sync(0xffffffffu, key, o), oq = __shfl_xor_sync(0xffffffffu, kq, o);
-            if (ok > key || (ok == key && oq < kq)) {
-                key = ok;
-                kq = oq;
-            }
-        }
+        // the half's argmax: the largest order key, then the smallest q among
+        // the lanes that hold it, by two reductions over the half's 16 lanes
+        // (each half waits only for its own lanes; both halves run them)
+        const uint32_t hmask = 0xffffu << (16 * h);
+        const uint32_t key = bq == NONE ? 0u : ord_key(best);
+        const uint32_t kmax = __reduce_max_sync(hmask, key);
+        const uint32_t kq = __reduce_min_sync(hmask, (key == kmax && bq != NONE) ? bq : NONE);
         const int bidx = kq < (uint32_t)NP ? (int)kq : NP / 2;  // no finite value: zero shift
         const int ky = bidx / ND - R, kx = bidx % ND - R;
         float c = 0.f;
