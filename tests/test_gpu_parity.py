@@ -167,6 +167,28 @@ def test_correlate_with_predictor_fp32(w, s, R, form, monkeypatch):
     check_fp32_pass(r, R)
 
 
+@pytest.mark.parametrize("form", ["tiles", "strips"])
+@pytest.mark.parametrize("w,s,R", [(64, 32, 4), (32, 16, 4), (16, 8, 4)])
+def test_correlate_peaks_at_the_search_edge(w, s, R, form, monkeypatch):
+    """A predictor R - 0.3 px short of the workload's analytic flow in x puts
+    the integer peaks on the edge of the +-R search, where the 5-point stencil
+    reaches shift R + 1 outside the plane: the direct FP32 stencil phase
+    (which a tile or strip step runs only when some window needs it) must then
+    match the oracle like the plane-supplied stencils."""
+    monkeypatch.setenv("RPIV_STRIP_MIN_CTAS", "1" if form == "strips" else str(1 << 40))
+    wk = wl.paper_1mp(W=320, H=288)
+    A, B = wk.render()
+    nx, ny = oracle.grid_n(320, w, s), oracle.grid_n(288, w, s)
+    X, Y = np.meshgrid(np.arange(nx) * s + 0.5 * (w - 1), np.arange(ny) * s + 0.5 * (w - 1))
+    fu, fv = wk.flow.eval(X, Y)
+    pu = np.asarray(fu, dtype=np.float64) - (R - 0.3)
+    pv = np.asarray(fv, dtype=np.float64)
+    r = compare_pass(A, B, w, s, R, pu, pv)
+    edge = r["valid"].astype(bool) & (np.abs(r["kx"]) == R)
+    assert edge.mean() >= 0.1, f"only {edge.mean():.3f} of the windows peak at the search edge"
+    check_fp32_pass(r, R)
+
+
 @pytest.mark.parametrize("kernel", ["tcgen05", "mma"])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 @pytest.mark.parametrize("w,s,R", [(64, 32, 4), (32, 16, 4), (16, 8, 4), (32, 8, 8), (48, 24, 6), (24, 12, 6)])
