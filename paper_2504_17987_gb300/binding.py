@@ -213,7 +213,10 @@ def _entry_ptrs(x, n: int):
 
 def _img_check(t: torch.Tensor, cfg_fmt: int, host: bool = False):
     if host:
-        if t.is_cuda or not t.is_pinned():
+        # that the memory is page-locked is checked by the library, once per
+        # image (rpiv_process_batch rejects it with a status and a message);
+        # a second driver query here would cost the serving loop per image
+        if t.is_cuda:
             raise ValueError("a host_frames engine takes pinned CPU tensors")
     elif not t.is_cuda:
         raise ValueError("images must be CUDA tensors")
